@@ -1,0 +1,179 @@
+/*
+ * relax.h -- C ABI of the GB300 (sm_103a) library that computes branch-and-bound
+ * node lower bounds for cardinality-constrained GLMs (arxiv 2603.01306).
+ *
+ * Problem (Sec. 2.3, Eq. 1):  min_beta f(X beta, y) + lambda2 ||beta||^2
+ *                              s.t. ||beta||_inf <= M, ||beta||_0 <= k.
+ * At a node N with fixings J0 (z = 0), J1 (z = 1) and free Jf, the library solves
+ * the perspective relaxation (Eq. 3-4) in its composite form (Eq. 6)
+ *     Phi(beta) = F(X beta) + 2 lambda2 g_N(beta)
+ * with FISTA and the duality-gap restart of Sec. 3.4, and returns
+ *     Psi(zeta) = -F*(-zeta) - G*(X' zeta)   (Eq. 7),  zeta = -grad F(X beta),
+ * which is a valid lower bound for the node by weak duality.
+ *
+ * Losses (the paper's formulas are in its missing appendix; this library's reading):
+ *   RELAX_LS:       F(z) = ||y - z||^2
+ *   RELAX_LOGISTIC: F(z) = sum_i log(1 + exp(-y_i z_i)),  y_i in {-1, +1}
+ *
+ * Conventions shared by every entry point
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller
+ *    (e.g. torch.Tensor.data_ptr()); the library never frees them.  Pointers
+ *    marked "host" are ordinary host memory.
+ *  - X is row-major with leading dimension ldx (elements), ldx >= p.
+ *  - fixings: device int8[p], -1 = J0, 0 = free (Jf), +1 = J1; NULL = root node.
+ *  - All device work is enqueued on the caller's stream (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  Entry points that return values in
+ *    host memory synchronize that stream before returning.
+ *  - Errors are returned as relax_status codes; nothing aborts or exits.  Invalid
+ *    arguments (k < |J1|, k < 0, lambda2 <= 0, M <= 0, n or p <= 0, null required
+ *    pointers) give RELAX_EINVAL and leave outputs untouched.
+ *  - Device-side waits are bounded by options.watchdog_ms; on expiry the kernel
+ *    records RELAX_ETIMEOUT and returns instead of spinning.
+ */
+#ifndef RELAX_H
+#define RELAX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct relax_handle relax_handle;
+
+typedef enum { RELAX_LS = 0, RELAX_LOGISTIC = 1 } relax_loss;
+
+typedef enum {
+  RELAX_F64 = 0,     /* double */
+  RELAX_F32 = 1,     /* float */
+  RELAX_BF16 = 2,    /* bfloat16 storage of X, per-column FP32 scales, FP32 accumulation */
+  RELAX_FP8E4M3 = 3  /* fp8 e4m3 storage of X, per-column FP32 scales, FP32 accumulation */
+} relax_dtype;
+
+typedef enum {
+  RELAX_OK = 0,
+  RELAX_EINVAL = 1,          /* invalid argument */
+  RELAX_ENOMEM = 2,          /* device allocation failed */
+  RELAX_ECUDA = 3,           /* a CUDA runtime call failed */
+  RELAX_ENOTCONV = 4,        /* max_iters reached before gap_tol (bounds still valid) */
+  RELAX_ETIMEOUT = 5,        /* a bounded device-side wait expired */
+  RELAX_ENUMERIC = 6,        /* NaN/Inf met in the data or the iterates */
+  RELAX_EINVALID_BOUND = 7,  /* certified dual bound above certified primal beyond rounding */
+  RELAX_ENOTSUP = 8          /* shape or option outside what this build supports */
+} relax_status;
+
+/* Solver options.  A zero-initialised struct means "all defaults". */
+typedef struct {
+  double M;            /* box bound of Eq. 1; 0 -> 2.0; +INFINITY allowed (no box) */
+  double eta;          /* restart factor of Sec. 3.4; 0 -> e^3 */
+  double lipschitz;    /* L of beta -> F(X beta); 0 -> power iteration at create */
+  int32_t max_iters;   /* 0 -> 100000 */
+  int32_t precision;   /* storage used for the in-loop X reads: 0 -> dtype of X;
+                          RELAX_BF16 / RELAX_FP8E4M3 require X in RELAX_F32 and make the
+                          handle keep a quantized copy (Sec. "precision" of the design) */
+  int32_t watchdog_ms; /* bound on any device-side wait; 0 -> 4000 */
+  int32_t no_certify;  /* 0 -> final FP64 evaluation of the bounds with the full X */
+  int32_t chunk;       /* iterations enqueued per host poll; 0 -> 32 */
+  int32_t timing;      /* 1 -> time every loop kernel with CUDA events on the handle's
+                          stream (fills xpass_ms / pphase_ms of relax_result); the host
+                          then waits for each chunk before enqueueing the next */
+  int32_t reserved[6];
+} relax_options;
+
+typedef struct {
+  double primal;       /* min Phi over the iterates (FP64-certified unless no_certify) */
+  double dual_bound;   /* max Psi: valid lower bound for the node (FP64-certified) */
+  double gap;          /* primal - dual_bound */
+  double rel_gap;      /* gap / max(1, |primal|) */
+  double primal_loop;  /* the same two values as tracked inside the loop, in the */
+  double dual_loop;    /* working precision of X */
+  double lipschitz;    /* L used (step = 1/L) */
+  int32_t iters;       /* prox steps taken */
+  int32_t restarts;    /* gap-based restarts */
+  int32_t status;      /* relax_status of the solve */
+  int32_t n_nz;        /* nonzeros of the returned beta */
+  int32_t launches;    /* CUDA kernels this call launched (incl. no-op tail of a chunk) */
+  int32_t xpass_count; /* fused X-passes that did work (iters + 1) */
+  double xpass_ms;     /* options.timing: summed device time of those X-passes */
+  double pphase_ms;    /* options.timing: summed device time of the p-phase launches */
+} relax_result;
+
+/* Create a solver handle bound to one design X and response y (Sec. 2.3).
+ *   X: device, row-major n x ldx, element type `dtype` (RELAX_F64 or RELAX_F32);
+ *      must stay alive and unchanged for the life of the handle.  Rows are read
+ *      with 16-byte bulk copies; when ldx*sizeof(elem) or X is not 16-byte
+ *      aligned the handle keeps an aligned internal copy.
+ *   y: device, n elements of `dtype` (copied into the handle).
+ *   k >= 1, lambda2 > 0; opt may be NULL (defaults).
+ * Computes L = c_f ||X||_2^2 (c_f = 2 for LS, 1/4 for logistic) by power
+ * iteration unless opt->lipschitz > 0.  Synchronizes `stream`. */
+relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_t n,
+                          int64_t p, int64_t ldx, int32_t dtype, int32_t loss, int32_t k,
+                          double lambda2, const relax_options* opt, void* stream);
+
+/* Solve the node relaxation (Eq. 3-4) to gap_tol relative duality gap
+ * ((Phi_best - Psi_best) / max(1, |Phi_best|)) with FISTA + gap restart (Sec. 3.4).
+ *   fixings: device int8[p] or NULL (root).
+ *   warm_start: device p elements of the handle's dtype or NULL (zero); any
+ *      vector is accepted (outside dom g_N the reference gap is taken at the
+ *      first iterate).
+ *   beta_out: device p elements of the handle's dtype: the primal point with the
+ *      smallest Phi seen.
+ *   out: host; filled on every return path after argument validation, including
+ *      RELAX_ENOTCONV / RELAX_ETIMEOUT (dual_bound stays a valid bound).
+ * Synchronizes the handle's stream. */
+relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* warm_start,
+                         double gap_tol, void* beta_out, relax_result* out);
+
+/* One fused pass over X (the matrix-vector products of Sec. 5.2.3 that dominate
+ * the method): z = X beta, r = grad F(z), g = X' r, read of X once.
+ *   beta: device p (handle dtype), z_out: device n (handle dtype),
+ *   g_out: device p (handle dtype), loss_host: host double[2] or NULL:
+ *   {F(z), -F*(r)} i.e. the primal loss and the loss part of Psi at zeta = -r.
+ * Synchronizes the handle's stream. */
+relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g_out,
+                         double* loss_host);
+
+/* FP64 evaluation of Phi(beta_primal) (Eq. 6) and Psi(zeta) (Eq. 7) at
+ * zeta = -grad F(X beta_dual), with the full-precision X (certification).
+ *   beta_primal, beta_dual: device p (handle dtype); fixings as in relax_solve.
+ *   out_host: host double[2] = {Phi, Psi}.  Phi is +inf when beta_primal is
+ *   outside dom g_N.  Synchronizes the handle's stream. */
+relax_status relax_certify(relax_handle* h, const int8_t* fixings, const void* beta_primal,
+                           const void* beta_dual, double* out_host);
+
+/* Release the handle and everything it allocated (not X, y, or caller buffers). */
+relax_status relax_destroy(relax_handle* h);
+
+/* prox of rho*g_N with rho = 2*lambda2*step (Algorithm 2 + Eq. prox:gN, Thm 4.5):
+ *   beta_out = argmin_u 0.5||u - beta_in||^2 + rho g_N(u).
+ *   beta_in, beta_out: device p elements of dtype (RELAX_F64 or RELAX_F32); may alias.
+ *   counts_out: device int32[2] or NULL: {n_top, n_nz} = free coordinates with
+ *      z_j = 1 (placed before the pooled block of Algorithm 2) and nonzero free
+ *      outputs.
+ * Uses stream-ordered scratch (cudaMallocAsync) on `stream`; does not synchronize. */
+relax_status prox_persp(const void* beta_in, void* beta_out, int64_t p, double step,
+                        int32_t k, double lambda2, double M, const int8_t* fixings,
+                        int32_t dtype, int32_t* counts_out, void* stream);
+
+/* g_N(beta) (Eq. 5; value of Algorithm 1 / Thm 4.4) into out_host[0]; +inf when
+ * beta is outside dom g_N (beyond a relative tolerance of 4 ulp of dtype).
+ *   beta: device p of dtype.  Synchronizes `stream`. */
+relax_status gval_persp(const void* beta, int64_t p, int32_t k, double M,
+                        const int8_t* fixings, int32_t dtype, double* out_host,
+                        void* stream);
+
+/* g_N*(alpha) = sum_J1 H_M(alpha_j) + TopSum_{k-|J1|} H_M(alpha_Jf)  (Lemma 4.2)
+ * into out_host[0].  alpha: device p of dtype.  Synchronizes `stream`. */
+relax_status gstar_persp(const void* alpha, int64_t p, int32_t k, double M,
+                         const int8_t* fixings, int32_t dtype, double* out_host,
+                         void* stream);
+
+/* Static, human-readable message for a status code. */
+const char* relax_strerror(relax_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELAX_H */

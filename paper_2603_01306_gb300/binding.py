@@ -1,0 +1,248 @@
+"""ctypes marshalling for the C ABI of ``include/relax.h``.
+
+Only argument marshalling lives here: tensors become device pointers, the
+current torch stream becomes the ``void* stream`` argument, C structs are
+mirrored with ctypes.  Status codes other than RELAX_OK raise ``RelaxError``
+(except where noted, where the code is returned with the result).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+RELAX_LS, RELAX_LOGISTIC = 0, 1
+RELAX_F64, RELAX_F32, RELAX_BF16, RELAX_FP8E4M3 = 0, 1, 2, 3
+STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA", 4: "RELAX_ENOTCONV",
+          5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
+
+EXPORTS = ["relax_create", "relax_solve", "relax_xpass", "relax_certify", "relax_destroy",
+           "prox_persp", "gval_persp", "gstar_persp", "relax_strerror"]
+
+
+class RelaxError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double), ("eta", ctypes.c_double), ("lipschitz", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("watchdog_ms", ctypes.c_int32), ("no_certify", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("primal", ctypes.c_double), ("dual_bound", ctypes.c_double), ("gap", ctypes.c_double),
+                ("rel_gap", ctypes.c_double), ("primal_loop", ctypes.c_double),
+                ("dual_loop", ctypes.c_double), ("lipschitz", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("n_nz", ctypes.c_int32), ("launches", ctypes.c_int32), ("xpass_count", ctypes.c_int32),
+                ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "librelax.so")
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.relax_create.argtypes = [ctypes.POINTER(vp), vp, vp, i64, i64, i64, i32, i32, i32, dbl,
+                                 ctypes.POINTER(Options), vp]
+    lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
+    lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_destroy.argtypes = [vp]
+    lib.prox_persp.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
+    lib.gval_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
+    lib.gstar_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
+    lib.relax_strerror.argtypes = [ctypes.c_int]
+    lib.relax_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS[:-1]:
+        getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points present in the shared library."""
+    lib = load()
+    return [n for n in EXPORTS if hasattr(lib, n)]
+
+
+def relax_strerror(code: int) -> str:
+    return load().relax_strerror(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise RelaxError(code, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return RELAX_F64
+    if t.dtype == torch.float32:
+        return RELAX_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must live on the GPU")
+
+
+def make_options(M=2.0, eta=0.0, lipschitz=0.0, max_iters=0, precision=0, watchdog_ms=0,
+                 certify=True, chunk=0, timing=False) -> Options:
+    o = Options()
+    o.M = float(M)
+    o.eta = float(eta)
+    o.lipschitz = float(lipschitz)
+    o.max_iters = int(max_iters)
+    o.precision = int(precision)
+    o.watchdog_ms = int(watchdog_ms)
+    o.no_certify = 0 if certify else 1
+    o.chunk = int(chunk)
+    o.timing = 1 if timing else 0
+    return o
+
+
+def relax_create(X, y, loss, k, lambda2, options: Options | None = None):
+    """relax_create: X (n x p, row-major, ldx = X.stride(0)) and y on the GPU."""
+    _need_cuda(X, y)
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a row-major 2-D tensor")
+    h = ctypes.c_void_p()
+    lib = load()
+    code = lib.relax_create(ctypes.byref(h), _ptr(X), _ptr(y), X.shape[0], X.shape[1], X.stride(0),
+                            _dtype_code(X), int(loss), int(k), float(lambda2),
+                            ctypes.byref(options) if options is not None else None, _stream(X.device))
+    _check(code, "relax_create")
+    return h
+
+
+def relax_solve(h, fixings, warm_start, gap_tol, beta_out):
+    """relax_solve; returns (status_code, Result) -- ENOTCONV etc. are not raised."""
+    _need_cuda(fixings, warm_start, beta_out)
+    res = Result()
+    code = load().relax_solve(h, _ptr(fixings), _ptr(warm_start), float(gap_tol), _ptr(beta_out),
+                              ctypes.byref(res))
+    if code in (1, 2, 3, 8):
+        raise RelaxError(code, "relax_solve")
+    return code, res
+
+
+def relax_xpass(h, beta, z_out, g_out):
+    _need_cuda(beta, z_out, g_out)
+    loss = (ctypes.c_double * 2)()
+    _check(load().relax_xpass(h, _ptr(beta), _ptr(z_out), _ptr(g_out), loss), "relax_xpass")
+    return float(loss[0]), float(loss[1])
+
+
+def relax_certify(h, fixings, beta_primal, beta_dual):
+    _need_cuda(fixings, beta_primal, beta_dual)
+    out = (ctypes.c_double * 2)()
+    _check(load().relax_certify(h, _ptr(fixings), _ptr(beta_primal), _ptr(beta_dual), out),
+           "relax_certify")
+    return float(out[0]), float(out[1])
+
+
+def relax_destroy(h):
+    _check(load().relax_destroy(h), "relax_destroy")
+
+
+def prox_persp(beta_in, beta_out, step, k, lambda2, M, fixings=None, counts_out=None):
+    _need_cuda(beta_in, beta_out, fixings, counts_out)
+    code = load().prox_persp(_ptr(beta_in), _ptr(beta_out), beta_in.numel(), float(step), int(k),
+                             float(lambda2), float(M), _ptr(fixings), _dtype_code(beta_in),
+                             _ptr(counts_out), _stream(beta_in.device))
+    _check(code, "prox_persp")
+
+
+def gval_persp(beta, k, M, fixings=None) -> float:
+    _need_cuda(beta, fixings)
+    out = ctypes.c_double()
+    _check(load().gval_persp(_ptr(beta), beta.numel(), int(k), float(M), _ptr(fixings),
+                             _dtype_code(beta), ctypes.byref(out), _stream(beta.device)),
+           "gval_persp")
+    return out.value
+
+
+def gstar_persp(alpha, k, M, fixings=None) -> float:
+    _need_cuda(alpha, fixings)
+    out = ctypes.c_double()
+    _check(load().gstar_persp(_ptr(alpha), alpha.numel(), int(k), float(M), _ptr(fixings),
+                              _dtype_code(alpha), ctypes.byref(out), _stream(alpha.device)),
+           "gstar_persp")
+    return out.value
+
+
+class Handle:
+    """Owns a relax_handle; X and y must outlive it."""
+
+    def __init__(self, X, y, loss="ls", k=10, lambda2=1.0, M=2.0, eta=0.0, lipschitz=0.0,
+                 max_iters=0, precision=0, certify=True, chunk=0, watchdog_ms=0, timing=False):
+        self.loss = {"ls": RELAX_LS, "logistic": RELAX_LOGISTIC}[loss] if isinstance(loss, str) else loss
+        self.X, self.y = X, y
+        self.n, self.p = X.shape
+        self.dtype = X.dtype
+        self.opts = make_options(M=M, eta=eta, lipschitz=lipschitz, max_iters=max_iters,
+                                 precision=precision, watchdog_ms=watchdog_ms, certify=certify,
+                                 chunk=chunk, timing=timing)
+        self.h = relax_create(X, y, self.loss, k, lambda2, self.opts)
+
+    def solve(self, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
+        import torch
+        if beta_out is None:
+            beta_out = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
+        code, res = relax_solve(self.h, fixings, warm_start, gap_tol, beta_out)
+        return beta_out, res, code
+
+    def xpass(self, beta):
+        import torch
+        z = torch.empty(self.n, dtype=self.dtype, device=self.X.device)
+        g = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
+        loss = relax_xpass(self.h, beta, z, g)
+        return z, g, loss
+
+    def certify(self, beta_primal, beta_dual=None, fixings=None):
+        return relax_certify(self.h, fixings, beta_primal,
+                             beta_primal if beta_dual is None else beta_dual)
+
+    def close(self):
+        if self.h is not None:
+            relax_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

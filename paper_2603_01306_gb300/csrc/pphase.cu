@@ -1,0 +1,46 @@
+// Instantiations and cooperative launch of the p-phase kernel.
+#include <algorithm>
+
+#include "launch.cuh"
+
+namespace relax {
+
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, bool gdouble, int64_t p) {
+  pl = PPlan{};
+  pl.vdouble = vdouble;
+  pl.gdouble = gdouble;
+  if (vdouble && gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<double, double>);
+  else if (!vdouble && gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<float, double>);
+  else if (!vdouble && !gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<float, float>);
+  else return cudaErrorNotSupported;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pl.kernel, PBLOCK, 0);
+  if (e != cudaSuccess) return e;
+  const int64_t maxgrid = (int64_t)nsm * std::max(per, 1);
+  // about two elements per thread; at most PEPT
+  const int64_t want = (p + 2 * PBLOCK - 1) / (2 * PBLOCK);
+  int64_t g = std::max<int64_t>(1, std::min<int64_t>(want, maxgrid));
+  if (g * PBLOCK * PEPT < p) g = (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT);
+  if (g > maxgrid) return cudaErrorNotSupported;
+  pl.grid = (int)g;
+  return cudaSuccess;
+}
+
+cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(pl.grid, 1, 1);
+  cfg.blockDim = dim3(PBLOCK, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[1] = {(void*)&a};
+  return cudaLaunchKernelExC(&cfg, pl.kernel, args);
+}
+
+}  // namespace relax

@@ -1,0 +1,674 @@
+// p-phase: everything an iteration does on p-vectors, in one cooperative launch.
+//
+//   P0  G^t = sum of the per-cluster X'r partials; a = -G^t/(2 lambda2) (the
+//       argument of g* in Psi, since X'zeta = -G^t); |beta^t| statistics.
+//   S1  TopSum_{kbar} H_M(|a_Jf|) of Lemma 4.2: exact kbar-th largest |a| by a
+//       radix select over the key bits (32 candidates per round, one per lane).
+//   S2  g_N(beta^t) (Thm 4.4 / Algorithm 1): the water level w of Algorithm 1
+//       is the root of sum_j min(|beta_j|, w) = kbar w; a multisection over the
+//       bits of w brackets it, an exact FP64 closed-form step finishes it:
+//       w = S_below / (kbar - N_above), g = (sum_J1 b^2 + sum_{|b|>w} b^2 + w S_below)/2.
+//   D   Phi, Psi, gap; best bounds; gap-based restart (Sec. 3.4); stop test.
+//   P1  v = y^t - s grad F at y^t (FISTA, Beck 2017 Sec. 10.7).
+//   S3  prox of rho g_N (Algorithm 2 + Eq. prox:gN).  The pooled block of
+//       Algorithm 2 is described by one threshold c >= 0: with
+//       w(c) = min(c/rho, M) and z_j(c) = min((|v_j| - c)_+ / w(c), 1), c is the
+//       root of sum_Jf z_j(c) = kbar (c = 0 when the budget is slack), and
+//          beta_j = sign(v_j) max(0, min(|v_j| - c, |v_j|/(1+rho), M))   on Jf,
+//       clip(v_j/(1+rho), +-M) on J1, 0 on J0.  Coordinates with z_j = 1 are the
+//       positions before the pooled block; those with 0 < z_j < 1 form the block.
+//       The root is bracketed by a multisection over the bits of c and finished
+//       by an exact FP64 closed form on the breakpoint-free piece:
+//          c = rho S_mid / (kbar - N_top + rho N_mid)           (c <= rho M)
+//          c = (S_mid - M (kbar - N_top)) / N_mid              (c >  rho M)
+//   P2  beta^{t+1}.
+//
+// Grid-wide steps use a bounded barrier (the grid is co-resident: cooperative
+// launch sized by occupancy).  Round counters are exact integer atomics (the
+// z-sums in 32.32 fixed point), so every block takes identical decisions; FP64
+// sums go through per-block partials summed in a fixed order (deterministic).
+#pragma once
+#include "common.cuh"
+#include "xpass.cuh"
+
+namespace relax {
+
+constexpr int PQ = 32;          // candidates per multisection round (one per lane)
+constexpr int PBLOCK = 256;
+constexpr int PNW = PBLOCK / 32;
+constexpr int PEPT = 4;         // max elements per thread
+constexpr int NFIELD = 8;       // round accumulator fields
+constexpr int ACC_STRIDE = NFIELD * PQ;
+constexpr int NBP = 8;          // doubles per block partial
+constexpr int MAX_POLISH = 8;
+
+enum PMode : int { PM_ITER = 0, PM_EVAL = 1, PM_PROX = 2, PM_GVAL = 3, PM_GSTAR = 4 };
+
+// accumulator fields
+enum : int { F_S1 = 0, F_S2Z = 1, F_S2C = 2, F_S3Z = 3, F_S3CM = 4, F_S3CT = 5, F_S3NZ = 6 };
+
+struct IterState {
+  PassState ps;                 // the pass's view; ps.beta == beta_cur
+  void* beta_prev;
+  void* beta_cur;
+  void* G_prev;
+  void* G_cur;
+  void* z_prev;
+  void* z_cur;
+  void* beta_best;              // argmin Phi so far
+  void* beta_dbest;             // beta whose induced zeta gave max Psi
+  double tau;                   // FISTA t_k
+  double gap_ref;               // gap at the start of the current restart epoch
+  double phi_best, psi_best;
+  double phi_t, psi_t, g_t, c_last;
+  int iter, restarts, have_ref, done, kbar, pbar, n_nz, n_top;
+  unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
+};
+
+struct PArgs {
+  int mode;
+  int loss;
+  int64_t p;
+  int k;                        // cardinality
+  double lambda2, M, step, rho, eta, tol;
+  int max_iters;
+  const int8_t* fix;            // NULL = root
+  const void* part;             // [ncl][NB][p] (ITER: TG=TV; EVAL: double)
+  int ncl, NB;
+  const double* lossp;          // [ncl][2]
+  IterState* st;
+  const void* vin;              // PROX: v; GVAL: beta; GSTAR: alpha; EVAL: beta_primal
+  void* vout;                   // PROX output
+  int* counts;                  // PROX: {n_top, n_nz}
+  double* out;                  // EVAL: {Phi, Psi}; GVAL: g; GSTAR: g*
+  unsigned long long* acc;      // [3][ACC_STRIDE], zero between launches
+  double* bpart;                // [2][gridDim][NBP]
+  unsigned long long* bar;      // grid barrier counter
+  unsigned long long bar_base;  // used when st == NULL
+  int* status;
+  uint64_t limit_ns;
+};
+
+template <typename T> __device__ __forceinline__ T huber_d(T a, T M) {
+  a = a < (T)0 ? -a : a;
+  return a <= M ? (T)0.5 * a * a : M * a - (T)0.5 * M * M;
+}
+
+template <typename KT>
+__device__ __forceinline__ KT cand(KT lo, KT hi, int q) {
+  // lo + 1 + floor((hi - lo - 1) (q+1) / (PQ+1)), strictly inside (lo, hi) when hi - lo >= 2
+  const KT d = hi - lo - 1;
+  const KT qq = (KT)(q + 1);
+  return lo + 1 + (d / (KT)(PQ + 1)) * qq + ((d % (KT)(PQ + 1)) * qq) / (KT)(PQ + 1);
+}
+
+__device__ __forceinline__ unsigned long long fixp(float z) {
+  return __float2ull_rz(z * 4294967296.0f);
+}
+__device__ __forceinline__ unsigned long long fixp(double z) {
+  return __double2ull_rz(z * 4294967296.0);
+}
+
+template <typename TV, typename TG>
+__global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
+  using KG = typename KeyOf<TG>::type;   // keys of |a| (S1)
+  using KV = typename KeyOf<TV>::type;   // keys of |beta| (S2) and of c (S3)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = gridDim.x * PBLOCK;
+  const int gt = blockIdx.x * PBLOCK + tid;
+  const int mode = a.mode;
+  IterState* st = a.st;
+
+  __shared__ unsigned long long red_u[PNW][NFIELD * PQ];
+  __shared__ unsigned long long sh_acc[NFIELD * PQ];
+  __shared__ double red_d[PNW][NBP];
+  __shared__ double sh_tot[NBP];
+  __shared__ int sh_done;
+
+  if (tid == 0) sh_done = (st != nullptr) ? st->done : 0;
+  __syncthreads();
+  if (sh_done) return;   // uniform: every block reads the same flag
+
+  const unsigned long long bar0 = st ? st->bar_base : a.bar_base;
+  int nbar = 0;
+  bool alive = true;
+  auto barrier = [&]() {
+    ++nbar;
+    if (alive && !grid_barrier(a.bar, bar0 + (unsigned long long)nbar * gridDim.x, a.limit_ns, a.status))
+      alive = false;
+  };
+  int nstep = 0;
+  // grid-wide deterministic FP64 sum of NV values
+  auto gsum = [&](double* v, int nv) {
+    double* bp = a.bpart + (size_t)(nstep & 1) * gridDim.x * NBP;
+    ++nstep;
+    for (int i = 0; i < nv; ++i) {
+      double s = warp_sum(v[i]);
+      if (lane == 0) red_d[warp][i] = s;
+    }
+    __syncthreads();
+    if (tid < nv) {
+      double s = 0.0;
+      for (int w = 0; w < PNW; ++w) s += red_d[w][tid];
+      bp[(size_t)blockIdx.x * NBP + tid] = s;
+    }
+    barrier();
+    if (warp < nv) {
+      double s = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(bp + (size_t)b * NBP + warp);
+      s = warp_sum(s);
+      if (lane == 0) sh_tot[warp] = s;
+    }
+    __syncthreads();
+    for (int i = 0; i < nv; ++i) v[i] = sh_tot[i];
+    __syncthreads();
+  };
+  int nround = 0;
+  // publish per-lane round fields (lane = candidate) and fetch the grid totals
+  auto round_reduce = [&](unsigned long long (&f)[NFIELD], int nf) {
+    unsigned long long* accb = a.acc + (size_t)(nround % 3) * ACC_STRIDE;
+    unsigned long long* accz = a.acc + (size_t)((nround + 1) % 3) * ACC_STRIDE;
+    ++nround;
+    for (int i = 0; i < nf; ++i) red_u[warp][i * PQ + lane] = f[i];
+    __syncthreads();
+    for (int t = tid; t < nf * PQ; t += PBLOCK) {
+      unsigned long long s = 0;
+      for (int w = 0; w < PNW; ++w) s += red_u[w][t];
+      if (s) atomicAdd(accb + t, s);
+    }
+    if (blockIdx.x == 0)
+      for (int t = tid; t < ACC_STRIDE; t += PBLOCK) accz[t] = 0ull;
+    barrier();
+    for (int t = tid; t < nf * PQ; t += PBLOCK) sh_acc[t] = __ldcg(accb + t);
+    __syncthreads();
+  };
+
+  const int64_t p = a.p;
+  const double M = a.M;
+  const double lam2 = a.lambda2;
+  const double rho = a.rho;
+  const TV Mv = (TV)M;
+
+  // ---------------------------------------------------------------- P0
+  const TV* bcur = nullptr;
+  const TV* bprev = nullptr;
+  const TG* Gprev = nullptr;
+  TG* Gcur = nullptr;
+  if (mode == PM_ITER) {
+    bcur = static_cast<const TV*>(st->beta_cur);
+    bprev = static_cast<const TV*>(st->beta_prev);
+    Gprev = static_cast<const TG*>(st->G_prev);
+    Gcur = static_cast<TG*>(st->G_cur);
+  } else if (mode == PM_EVAL || mode == PM_GVAL) {
+    bcur = static_cast<const TV*>(a.vin);
+  }
+  const TG* part = static_cast<const TG*>(a.part);
+
+  int8_t fx[PEPT];
+  KG ka[PEPT];        // S1 keys: |a| on Jf, 0 elsewhere
+  TV bm[PEPT];        // S2: |beta| on Jf, 0 elsewhere
+  TV bt[PEPT];        // beta^t
+  TG gg[PEPT];        // G^t
+  TG gy[PEPT];        // logistic: X' grad F at the tentative y^t
+  // sums: 0 sum_J1 H(a), 1 sum_J1 b^2, 2 sum_Jf |b|, 3 sum_Jf b^2, 4 nnz_Jf(b),
+  //       5 domain violations, 6 non-finite, 7 sum_Jf H(a)
+  double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const bool need_a = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GSTAR);
+  const bool need_b = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GVAL);
+#pragma unroll
+  for (int e = 0; e < PEPT; ++e) {
+    const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+    fx[e] = 0; ka[e] = 0; bm[e] = (TV)0; bt[e] = (TV)0; gg[e] = (TG)0; gy[e] = (TG)0;
+    if (j >= p) { fx[e] = -2; continue; }
+    const int8_t f = a.fix ? a.fix[j] : (int8_t)0;
+    fx[e] = f;
+    if (need_a) {
+      TG av;
+      if (mode == PM_GSTAR) {
+        av = static_cast<const TG*>(a.vin)[j];
+      } else {
+        TG G = (TG)0, Gy = (TG)0;
+        for (int c = 0; c < a.ncl; ++c) {
+          G += part[((int64_t)c * a.NB) * p + j];
+          if (a.NB > 1) Gy += part[((int64_t)c * a.NB + 1) * p + j];
+        }
+        gg[e] = G;
+        gy[e] = Gy;
+        if (mode == PM_ITER) Gcur[j] = G;
+        av = -G / (TG)(2.0 * lam2);
+      }
+      if (!isfinite((double)av)) s0[6] += 1.0;
+      const TG aa = av < (TG)0 ? -av : av;
+      if (f > 0) s0[0] += (double)huber_d<TG>(aa, (TG)M);
+      if (f == 0) { ka[e] = key_of(aa); s0[7] += (double)huber_d<TG>(aa, (TG)M); }
+    }
+    if (need_b) {
+      const TV b = bcur[j];
+      bt[e] = b;
+      if (!isfinite((double)b)) s0[6] += 1.0;
+      const TV ab = b < (TV)0 ? -b : b;
+      if (f > 0) { s0[1] += (double)b * (double)b; if ((double)ab > M * (1.0 + 1e-6)) s0[5] += 1.0; }
+      else if (f < 0) { if (b != (TV)0) s0[5] += 1.0; }
+      else {
+        bm[e] = ab;
+        s0[2] += (double)ab;
+        s0[3] += (double)ab * (double)ab;
+        if (ab > (TV)0) s0[4] += 1.0;
+        if ((double)ab > M * (1.0 + 1e-6)) s0[5] += 1.0;
+      }
+    }
+  }
+  const int kbar = st ? st->kbar : 0;   // filled below for the standalone modes
+  int kb = kbar, pb = st ? st->pbar : 0;
+  double tot[NBP];
+  for (int i = 0; i < NBP; ++i) tot[i] = s0[i];
+  // standalone modes need |J1| and |Jf|; reuse the sum for counts
+  double cnt2[2] = {0, 0};
+  if (!st) {
+    for (int e = 0; e < PEPT; ++e) {
+      if (fx[e] > 0) cnt2[0] += 1.0;
+      if (fx[e] == 0) cnt2[1] += 1.0;
+    }
+  }
+  gsum(tot, NBP);
+  if (!st) {
+    gsum(cnt2, 2);
+    kb = a.k - (int)cnt2[0];
+    pb = (int)cnt2[1];
+  }
+  (void)kbar;
+  const double Ftot = [&]() {
+    double s = 0.0;
+    if (a.lossp) for (int c = 0; c < a.ncl; ++c) s += a.lossp[c * 2 + 0];
+    return s;
+  }();
+  const double Dtot = [&]() {
+    double s = 0.0;
+    if (a.lossp) for (int c = 0; c < a.ncl; ++c) s += a.lossp[c * 2 + 1];
+    return s;
+  }();
+  const bool nonfinite = tot[6] > 0.0;
+
+  // ------------------------------------------------------ S1 / S2 setup
+  bool s1 = false, s2 = false;
+  double topsum = 0.0, gval = 0.0;
+  KG lo1 = 0, hi1 = (KG)(KeyOf<TG>::kInf + 1);
+  KV lo2 = 0, hi2 = (KV)KeyOf<TV>::kInf;
+  double c2lo = 0.0, c2hi = 0.0;   // #{|b| > lo2}, #{|b| > hi2}
+  if (need_a) {
+    if (kb <= 0) topsum = 0.0;
+    else if (pb <= kb) topsum = tot[7];
+    else s1 = true;
+  }
+  bool g_inf = false;
+  if (need_b) {
+    const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
+    if (check_dom && (tot[5] > 0.0 || (kb > 0 && tot[2] > M * (double)kb * (1.0 + 1e-6)) ||
+                      (kb <= 0 && tot[2] > 0.0)))
+      g_inf = true;
+    if (g_inf) gval = INFINITY;
+    else if (kb <= 0) gval = 0.5 * tot[1];
+    else if (tot[4] <= (double)kb) gval = 0.5 * (tot[1] + tot[3]);
+    else { s2 = true; c2lo = tot[4]; c2hi = 0.0; }
+  }
+
+  // ------------------------------------------------------- S1 / S2 rounds
+  while (s1 || s2) {
+    unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const KG x1 = s1 ? cand<KG>(lo1, hi1, lane) : (KG)0;
+    const KV x2 = s2 ? cand<KV>(lo2, hi2, lane) : (KV)0;
+    const TV w2 = from_key(x2, (TV)0);
+    const TV inv2 = s2 ? (TV)1 / w2 : (TV)0;
+    for (int src = 0; src < 32; ++src) {
+#pragma unroll
+      for (int e = 0; e < PEPT; ++e) {
+        if (s1) {
+          const KG kv = __shfl_sync(0xffffffffu, ka[e], src);
+          fld[F_S1] += (kv >= x1) ? 1ull : 0ull;
+        }
+        if (s2) {
+          const TV b = __shfl_sync(0xffffffffu, bm[e], src);
+          if (b > (TV)0) {
+            const TV z = b * inv2;
+            fld[F_S2Z] += fixp(z < (TV)1 ? z : (TV)1);
+            fld[F_S2C] += (b > w2) ? 1ull : 0ull;
+          }
+        }
+      }
+    }
+    round_reduce(fld, 3);
+    if (s1) {
+      // largest candidate with count >= kb -> new lo; smallest with count < kb -> new hi
+      KG nlo = lo1, nhi = hi1;
+      for (int q = 0; q < PQ; ++q) {
+        const KG xq = cand<KG>(lo1, hi1, q);
+        if (sh_acc[F_S1 * PQ + q] >= (unsigned long long)kb) { if (xq > nlo) nlo = xq; }
+        else if (xq < nhi) nhi = xq;
+      }
+      lo1 = nlo; hi1 = nhi;
+      if (hi1 - lo1 <= 1) s1 = false;
+    }
+    if (s2) {
+      KV nlo = lo2, nhi = hi2;
+      double nclo = c2lo, nchi = c2hi;
+      const unsigned long long thr = (unsigned long long)kb << 32;
+      for (int q = 0; q < PQ; ++q) {
+        const KV xq = cand<KV>(lo2, hi2, q);
+        const double cq = (double)sh_acc[F_S2C * PQ + q];
+        if (sh_acc[F_S2Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nclo = cq; } }
+        else if (xq < nhi) { nhi = xq; nchi = cq; }
+      }
+      lo2 = nlo; hi2 = nhi; c2lo = nclo; c2hi = nchi;
+      if (c2lo == c2hi || hi2 - lo2 <= 1) s2 = false;
+    }
+  }
+
+  // ---------------------------------------------- exact S1 / S2 finishing
+  // S1: t* = the kbar-th largest |a| (key lo1); TopSum = sum_{|a|>t*} H + (kbar - N_>) H(t*)
+  // S2: w on the bracket's piece; polished until the classification is stable.
+  const bool fin1 = need_a && kb > 0 && pb > kb;
+  bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb;
+  double wcur = pol2 ? (double)from_key(hi2, (TV)0) : 0.0;
+  double nprev = -1.0;
+  const double wlo = (double)from_key(lo2, (TV)0), whi = (double)from_key(hi2, (TV)0);
+  int npol = 0;
+  bool first = true;
+  while (first || pol2) {
+    double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = 0; e < PEPT; ++e) {
+      if (first && fin1 && fx[e] == 0 && ka[e] > lo1) {
+        v[0] += (double)huber_d<TG>(from_key(ka[e], (TG)0), (TG)M);
+        v[1] += 1.0;
+      }
+      if (pol2 && (double)bm[e] > wcur) {
+        v[2] += 1.0;
+        v[3] += (double)bm[e];
+        v[4] += (double)bm[e] * (double)bm[e];
+      }
+    }
+    gsum(v, 5);
+    if (first && fin1) {
+      const double tstar = (double)from_key(lo1, (TG)0);
+      topsum = v[0] + ((double)kb - v[1]) * huber_d<double>(tstar, M);
+    }
+    first = false;
+    if (pol2) {
+      // classification at wcur: N_above, S_above, Q_above
+      const double Nab = v[2], Sab = v[3], Qab = v[4];
+      const double Sbel = tot[2] - Sab;
+      const double wn = Sbel / ((double)kb - Nab);
+      const bool stable = (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
+      if (stable || npol >= MAX_POLISH) {
+        gval = 0.5 * (tot[1] + Qab + wn * Sbel);
+        pol2 = false;
+      } else {
+        nprev = Nab;
+        wcur = wn;
+        ++npol;
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- D
+  double phi = 0.0, psi = 0.0;
+  if (mode == PM_ITER || mode == PM_EVAL) {
+    phi = Ftot + 2.0 * lam2 * gval;
+    psi = Dtot - 2.0 * lam2 * (tot[0] + topsum);
+  }
+  if (mode == PM_EVAL) {
+    if (blockIdx.x == 0 && tid == 0) {
+      a.out[0] = phi;
+      a.out[1] = psi;
+      if (nonfinite) atomicCAS(a.status, ST_OK, ST_NUMERIC);
+    }
+  } else if (mode == PM_GVAL) {
+    if (blockIdx.x == 0 && tid == 0) a.out[0] = gval;
+  } else if (mode == PM_GSTAR) {
+    if (blockIdx.x == 0 && tid == 0) a.out[0] = tot[0] + topsum;
+  }
+
+  bool stop = false, restart = false, imp_p = false, imp_d = false;
+  double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
+  int have_ref = 0, restarts = 0;
+  const int t = st ? st->iter : 0;
+  if (mode == PM_ITER) {
+    const double tau = st->tau;
+    gap_ref = st->gap_ref;
+    have_ref = st->have_ref;
+    phi_best = st->phi_best;
+    psi_best = st->psi_best;
+    restarts = st->restarts;
+    if (nonfinite) stop = true;
+    if (phi < phi_best) { phi_best = phi; imp_p = true; }
+    if (psi > psi_best) { psi_best = psi; imp_d = true; }
+    const double gap = phi - psi;
+    if (!have_ref) {
+      if (isfinite(gap)) { gap_ref = gap; have_ref = 1; }
+    } else if (t >= 1 && gap <= gap_ref / a.eta) {
+      restart = true;
+      gap_ref = gap;
+      ++restarts;
+    }
+    if (t == 0) { mu = 0.0; tau_new = tau; }
+    else if (restart) { mu = 0.0; tau_new = 1.0; }
+    else {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau * tau));
+      mu = (tau - 1.0) / tn;
+      tau_new = tn;
+    }
+    if (isfinite(phi_best) && phi_best - psi_best <= a.tol * fmax(1.0, fabs(phi_best))) stop = true;
+    if (t >= a.max_iters) stop = true;
+  }
+
+  // best iterates (also on the stopping iteration)
+  if (mode == PM_ITER && (imp_p || imp_d)) {
+    TV* bbest = static_cast<TV*>(st->beta_best);
+    TV* bdbest = static_cast<TV*>(st->beta_dbest);
+#pragma unroll
+    for (int e = 0; e < PEPT; ++e) {
+      const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+      if (j >= p) continue;
+      if (imp_p) bbest[j] = bt[e];
+      if (imp_d) bdbest[j] = bt[e];
+    }
+  }
+
+  // ---------------------------------------------------------------- P1
+  const bool do_prox = (mode == PM_PROX) || (mode == PM_ITER && !stop);
+  TV vv[PEPT];
+  TV mm[PEPT];      // |v| on Jf
+  TV ti[PEPT];      // T^{-1}(|v|): where coordinate j reaches z_j = 1
+  double nzv = 0.0;
+  if (do_prox) {
+    const TV* vin = static_cast<const TV*>(a.vin);
+    const TV muv = (TV)mu;
+    const TV sv = (TV)a.step;
+#pragma unroll
+    for (int e = 0; e < PEPT; ++e) {
+      const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+      vv[e] = (TV)0; mm[e] = (TV)0; ti[e] = (TV)0;
+      if (j >= p) continue;
+      TV v;
+      if (mode == PM_ITER) {
+        const TV b = bt[e];
+        const TV bp = bprev[j];
+        const TV y = b + muv * (b - bp);
+        TG gyv;
+        if (a.loss == 0) gyv = ((TG)1 + (TG)mu) * gg[e] - (TG)mu * Gprev[j];
+        else gyv = (mu == 0.0) ? gg[e] : gy[e];
+        v = y - sv * (TV)gyv;
+      } else {
+        v = vin[j];
+      }
+      vv[e] = v;
+      if (fx[e] == 0) {
+        const TV m = v < (TV)0 ? -v : v;
+        mm[e] = m;
+        const double md = (double)m;
+        ti[e] = (TV)((md <= M * (1.0 + rho)) ? md * (rho / (1.0 + rho)) : md - M);
+        if (m > (TV)0) nzv += 1.0;
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- S3
+  double c = 0.0;
+  int n_top = 0, n_nz = 0;
+  if (do_prox) {
+    gsum(&nzv, 1);
+    bool s3 = false;
+    KV lo3 = 0, hi3 = (KV)KeyOf<TV>::kInf;
+    double cmlo = nzv, cmhi = 0.0, ctlo = nzv, cthi = 0.0;   // #{m > lo}, #{m > hi}, same for T^-1
+    if (kb <= 0) c = INFINITY;
+    else if (nzv <= (double)kb) c = 0.0;
+    else s3 = true;
+    const double rhoM = rho * M;
+    while (s3) {
+      unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const KV x3 = cand<KV>(lo3, hi3, lane);
+      const TV cq = from_key(x3, (TV)0);
+      const double cqd = (double)cq;
+      const double wq = fmin(cqd / rho, M);
+      const TV invw = (TV)(1.0 / wq);
+      for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int e = 0; e < PEPT; ++e) {
+          const TV m = __shfl_sync(0xffffffffu, mm[e], src);
+          const TV tv = __shfl_sync(0xffffffffu, ti[e], src);
+          if (m > cq) {
+            const TV z = (m - cq) * invw;
+            fld[F_S3Z] += fixp(z < (TV)1 ? z : (TV)1);
+            fld[F_S3CM] += 1ull;
+          }
+          fld[F_S3CT] += (tv > cq) ? 1ull : 0ull;
+        }
+      }
+      // fields 3..5 live at indices F_S3Z.. ; reduce fields 0..5 (0..2 unused here)
+      round_reduce(fld, 6);
+      KV nlo = lo3, nhi = hi3;
+      double nmlo = cmlo, nmhi = cmhi, ntlo = ctlo, nthi = cthi;
+      const unsigned long long thr = (unsigned long long)kb << 32;
+      for (int q = 0; q < PQ; ++q) {
+        const KV xq = cand<KV>(lo3, hi3, q);
+        const double cm = (double)sh_acc[F_S3CM * PQ + q], ct = (double)sh_acc[F_S3CT * PQ + q];
+        if (sh_acc[F_S3Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nmlo = cm; ntlo = ct; } }
+        else if (xq < nhi) { nhi = xq; nmhi = cm; nthi = ct; }
+      }
+      lo3 = nlo; hi3 = nhi; cmlo = nmlo; cmhi = nmhi; ctlo = ntlo; cthi = nthi;
+      const double clo = (double)from_key(lo3, (TV)0), chi = (double)from_key(hi3, (TV)0);
+      const bool regime_inside = (rhoM > clo && rhoM <= chi);
+      if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
+    }
+    if (kb > 0 && nzv > (double)kb) {
+      // exact finishing on the bracket's piece, polished until stable
+      const double clo = (double)from_key(lo3, (TV)0), chi = (double)from_key(hi3, (TV)0);
+      double ccur = chi;
+      double ntop_prev = -1.0, nmid_prev = -1.0;
+      for (int it = 0; it <= MAX_POLISH; ++it) {
+        const double Tc = (ccur <= rhoM) ? ccur * (1.0 + rho) / rho : ccur + M;
+        double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int e = 0; e < PEPT; ++e) {
+          if (fx[e] != 0) continue;
+          const double m = (double)mm[e];
+          if (m >= Tc) v[0] += 1.0;
+          else if (m > ccur) { v[1] += 1.0; v[2] += m; }
+        }
+        gsum(v, 3);
+        const double Ntop = v[0], Nmid = v[1], Smid = v[2];
+        double cn;
+        if (Nmid == 0.0) cn = ccur;   // flat piece: any c on it is a root when Ntop == kbar
+        else if (ccur <= rhoM) cn = rho * Smid / ((double)kb - Ntop + rho * Nmid);
+        else cn = (Smid - M * ((double)kb - Ntop)) / Nmid;
+        const bool inside = (it == 0) && cn > clo && cn <= chi && cmlo == cmhi && ctlo == cthi &&
+                            !(rhoM > clo && rhoM <= chi);
+        const bool stable = (Ntop == ntop_prev && Nmid == nmid_prev);
+        if (inside || stable || it == MAX_POLISH || !(cn > 0.0) || !isfinite(cn)) {
+          c = (isfinite(cn) && cn > 0.0) ? cn : ccur;
+          break;
+        }
+        ntop_prev = Ntop; nmid_prev = Nmid;
+        ccur = cn;
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- P2
+  if (do_prox) {
+    TV* out = mode == PM_ITER ? static_cast<TV*>(st->beta_prev) : static_cast<TV*>(a.vout);
+    const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
+    double cnt[2] = {0, 0};
+#pragma unroll
+    for (int e = 0; e < PEPT; ++e) {
+      const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+      if (j >= p) continue;
+      const double v = (double)vv[e];
+      double b;
+      if (fx[e] < 0) b = 0.0;
+      else if (fx[e] > 0) b = fmin(fmax(v / (1.0 + rho), -M), M);
+      else {
+        const double m = fabs(v);
+        const double r = fmax(0.0, fmin(fmin(m - c, m / (1.0 + rho)), M));
+        b = v < 0.0 ? -r : r;
+        if (r > 0.0) {
+          cnt[1] += 1.0;
+          if (m >= T_c) cnt[0] += 1.0;
+        }
+      }
+      out[j] = (TV)b;
+    }
+    if (mode == PM_PROX && a.counts) {
+      gsum(cnt, 2);
+      if (blockIdx.x == 0 && tid == 0) {
+        a.counts[0] = (int)cnt[0];
+        a.counts[1] = (int)cnt[1];
+      }
+    }
+  }
+
+  // ------------------------------------------------------------- epilogue
+  barrier();   // everyone is done with the round accumulators
+  if (blockIdx.x == 0) {
+    for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
+    if (tid == 0) {
+      if (mode == PM_ITER) {
+        if (nonfinite) atomicCAS(a.status, ST_OK, ST_NUMERIC);
+        st->phi_t = phi;
+        st->psi_t = psi;
+        st->g_t = gval;
+        st->phi_best = phi_best;
+        st->psi_best = psi_best;
+        st->gap_ref = gap_ref;
+        st->have_ref = have_ref;
+        st->restarts = restarts;
+        st->c_last = c;
+        if (stop) {
+          st->done = 1;
+          st->ps.done = 1;
+        } else {
+          // rotate: beta_prev <- beta^t, beta_cur <- beta^{t+1} (written into the old prev)
+          void* b_old_prev = st->beta_prev;
+          st->beta_prev = st->beta_cur;
+          st->beta_cur = b_old_prev;
+          void* g_old_prev = st->G_prev;
+          st->G_prev = st->G_cur;
+          st->G_cur = g_old_prev;
+          void* z_old_prev = st->z_prev;
+          st->z_prev = st->z_cur;
+          st->z_cur = z_old_prev;
+          st->tau = tau_new;
+          st->iter = t + 1;
+          st->ps.beta = st->beta_cur;
+          st->ps.zout = st->z_cur;
+          st->ps.zprev = st->z_prev;
+          // tentative momentum for the pass at beta^{t+1} (the no-restart value)
+          const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau_new * tau_new));
+          st->ps.mom = (tau_new - 1.0) / tn;
+        }
+        st->bar_base = bar0 + (unsigned long long)nbar * gridDim.x;
+      }
+    }
+  }
+  (void)n_top; (void)n_nz;
+}
+
+}  // namespace relax
