@@ -172,6 +172,10 @@ relax_status gstar_persp(const void* alpha, int64_t p, int32_t k, double M,
 /* Static, human-readable message for a status code. */
 const char* relax_strerror(relax_status s);
 
+/* Thread-local description of the last failing CUDA runtime call made by this
+ * library in the calling thread (empty when none); valid until the next call. */
+const char* relax_error_detail(void);
+
 #ifdef __cplusplus
 }
 #endif

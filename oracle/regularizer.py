@@ -56,15 +56,15 @@ def in_domain(beta, fix, k, M, rtol=0.0):
 DOMAIN_RTOL = 1e-12
 
 
-def g_alg1(beta, fix, k, M):
+def g_alg1(beta, fix, k, M, domain_rtol=DOMAIN_RTOL):
     """g_N(beta) by Algorithm 1 (Thm 4.4); +inf outside dom g_N.
 
-    Points within DOMAIN_RTOL (relative) of the box or l1 boundary count as on
+    Points within domain_rtol (relative) of the box or l1 boundary count as on
     it, so that rounding of a boundary point does not make g infinite.
     """
     beta = np.asarray(beta, dtype=np.float64)
     fix, J0, J1, Jf = _sets(fix, beta.size)
-    if not in_domain(beta, fix, k, M, rtol=DOMAIN_RTOL):
+    if not in_domain(beta, fix, k, M, rtol=domain_rtol):
         return math.inf
     kbar = k - J1.size
     pbar = Jf.size

@@ -16,7 +16,7 @@ STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA",
           5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
 
 EXPORTS = ["relax_create", "relax_solve", "relax_xpass", "relax_certify", "relax_destroy",
-           "prox_persp", "gval_persp", "gstar_persp", "relax_strerror"]
+           "prox_persp", "gval_persp", "gstar_persp", "relax_strerror", "relax_error_detail"]
 
 
 class RelaxError(RuntimeError):
@@ -73,7 +73,9 @@ def load():
     lib.gstar_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
     lib.relax_strerror.argtypes = [ctypes.c_int]
     lib.relax_strerror.restype = ctypes.c_char_p
-    for name in EXPORTS[:-1]:
+    lib.relax_error_detail.argtypes = []
+    lib.relax_error_detail.restype = ctypes.c_char_p
+    for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -89,9 +91,14 @@ def relax_strerror(code: int) -> str:
     return load().relax_strerror(code).decode()
 
 
+def relax_error_detail() -> str:
+    return load().relax_error_detail().decode()
+
+
 def _check(code: int, what: str):
     if code != 0:
-        raise RelaxError(code, what)
+        detail = relax_error_detail()
+        raise RelaxError(code, f"{what} ({detail})" if detail else what)
 
 
 def _ptr(t):
@@ -154,7 +161,7 @@ def relax_solve(h, fixings, warm_start, gap_tol, beta_out):
     code = load().relax_solve(h, _ptr(fixings), _ptr(warm_start), float(gap_tol), _ptr(beta_out),
                               ctypes.byref(res))
     if code in (1, 2, 3, 8):
-        raise RelaxError(code, "relax_solve")
+        _check(code, "relax_solve")
     return code, res
 
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -17,10 +18,19 @@ using namespace relax;
 
 namespace {
 
-#define CU(call)                                  \
-  do {                                            \
-    cudaError_t e_ = (call);                      \
-    if (e_ != cudaSuccess) return map_cuda(e_);   \
+thread_local char g_detail[256] = "";
+
+void set_detail(const char* what, cudaError_t e, int line) {
+  snprintf(g_detail, sizeof(g_detail), "%s failed: %s (api.cu:%d)", what, cudaGetErrorString(e), line);
+}
+
+#define CU(call)                                                \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) {                                    \
+      set_detail(#call, e_, __LINE__);                          \
+      return map_cuda(e_);                                      \
+    }                                                           \
   } while (0)
 
 relax_status map_cuda(cudaError_t e) {
@@ -55,17 +65,32 @@ __global__ void count_fix_kernel(const int8_t* fix, int64_t p, int* out) {
   }
 }
 
-template <typename T>
-__global__ void init_vectors_kernel(const T* warm, T* b0, T* b1, T* bb, T* bd, T* g0, T* g1, int64_t p,
-                                    T* z0, T* z1, int64_t n) {
+// loop vectors are FP64; caller vectors are in the handle's dtype
+__global__ void init_vectors_kernel(const void* warm, int warm_f64, double* b0, double* b1, double* bb, double* bd,
+                                    double* g0, double* g1, int64_t p, double* z0, double* z1, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += stride) {
-    const T w = warm ? warm[j] : (T)0;
+    double w = 0.0;
+    if (warm) w = warm_f64 ? static_cast<const double*>(warm)[j] : (double)static_cast<const float*>(warm)[j];
     b0[j] = w; b1[j] = w; bb[j] = w; bd[j] = w;
-    g0[j] = (T)0; g1[j] = (T)0;
+    g0[j] = 0.0; g1[j] = 0.0;
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    z0[i] = (T)0; z1[i] = (T)0;
+    z0[i] = 0.0; z1[i] = 0.0;
+  }
+}
+
+// dst (double) <- src (float or double)
+__global__ void to_f64_kernel(const void* src, int src_f64, double* dst, int64_t m) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = src_f64 ? static_cast<const double*>(src)[j] : (double)static_cast<const float*>(src)[j];
+}
+
+// dst (float or double) <- src (double)
+__global__ void from_f64_kernel(const double* src, void* dst, int dst_f64, int64_t m) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    if (dst_f64) static_cast<double*>(dst)[j] = src[j];
+    else static_cast<float*>(dst)[j] = (float)src[j];
   }
 }
 
@@ -99,11 +124,36 @@ __global__ void scale_kernel(T* v, int64_t p, const double* sq) {
     v[j] *= inv;
 }
 
-template <typename T>
-__global__ void nnz_kernel(const T* v, int64_t p, int* out) {
+__global__ void sumsq_kernel(const double* v, int64_t m, double* out) {
+  double s = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    s += v[j] * v[j];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+}
+
+// {F(z), -F*(-zeta)} at zeta = -grad F(z) (Eq. 6-7 loss parts), FP64
+__global__ void loss_terms_kernel(const double* z, const double* y, int64_t n, int loss, double* out) {
+  double f = 0.0, d = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (loss == RELAX_LS) {
+      const double r = z[i] - y[i], zeta = -2.0 * r;
+      f += r * r;
+      d += zeta * y[i] - 0.25 * zeta * zeta;
+    } else {
+      f += softplus_neg(y[i] * z[i]);
+      d += entropy_of(y[i] * z[i]);
+    }
+  }
+  f = warp_sum(f);
+  d = warp_sum(d);
+  if ((threadIdx.x & 31) == 0) { atomicAdd(out, f); atomicAdd(out + 1, d); }
+}
+
+__global__ void nnz_kernel(const double* v, int64_t p, int* out) {
   int c = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
-    c += v[j] != (T)0;
+    c += v[j] != 0.0;
   c = warp_sum(c);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
@@ -175,15 +225,18 @@ struct relax_handle {
   int xk_loop = XK_F32;
   void* y = nullptr;
   // plans
-  XPlan pl_loop, pl_cert, pl_ident;
+  XBPlan pl_loop, pl_cert, pl_certz, pl_ident;
   PPlan pp_iter, pp_eval;
   // buffers
-  void* part_loop = nullptr;
-  void* part_cert = nullptr;
-  double* lossp = nullptr;
+  double* xpart = nullptr;       // [n][nchunk][NF] row-chunk partials of the pass
+  double* xr = nullptr;          // [2][n] link values
+  double* xg = nullptr;          // [2][p] X' r
+  double* lterm = nullptr;       // [n][2] certification loss terms
+  unsigned* xcnt = nullptr;      // pass counters: done[nblk] | bdone[nblk] | rowcnt[n]
   IterState* st = nullptr;
   PassState* ps_aux = nullptr;
-  void* vb[8] = {};          // beta prev/cur, G prev/cur, beta_best, beta_dbest, z prev/cur
+  void* vb[13] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
+                             // z prev/cur (n); scratch p, p, n, n; z of the best dual (n)
   unsigned long long* acc = nullptr;
   double* bpart = nullptr;
   unsigned long long* bar = nullptr;
@@ -196,6 +249,7 @@ struct relax_handle {
   double* h_d = nullptr;         // pinned doubles
   int* h_i = nullptr;            // pinned ints
   size_t esz() const { return dtype == RELAX_F64 ? 8 : 4; }
+  int f64() const { return dtype == RELAX_F64 ? 1 : 0; }
 };
 
 namespace {
@@ -204,7 +258,7 @@ void handle_free(relax_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->part_loop, h->part_cert, h->lossp, h->st,
+  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xpart, h->xr, h->xg, h->lterm, h->xcnt, h->st,
                   h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (void* q : h->vb) if (q) cudaFree(q);
@@ -221,27 +275,41 @@ relax_status alloc(void** p, size_t bytes) {
   return RELAX_OK;
 }
 
-XPassArgs pass_args(relax_handle* h, const XPlan& pl, int link, PassState* ps, void* part) {
-  XPassArgs a{};
+XBArgs pass_args(relax_handle* h, const XBPlan& pl, int link, PassState* ps) {
+  XBArgs a{};
   const bool lowp = (pl.xk == XK_BF16 || pl.xk == XK_FP8);
   a.X = lowp ? h->Xq : h->X;
   a.ldx = lowp ? h->ldq : h->ldx;
   a.n = h->n;
   a.p = h->p;
-  a.slice = pl.slice;
-  a.C = pl.C;
-  a.R = pl.R;
-  a.S = pl.S;
-  a.slot_bytes = pl.slot_bytes;
+  a.cw = pl.cw;
+  a.nchunk = pl.nchunk;
+  a.B = pl.B;
+  a.nblk = pl.nblk;
+  a.lag = pl.lag;
+  a.sw = pl.sw;
+  a.beta_smem = pl.beta_smem;
   a.link = link;
-  a.y = h->y;
+  a.y = (const double*)h->y;
   a.colscale = lowp ? h->colscale : nullptr;
   a.ps = ps;
-  a.part = part;
-  a.lossp = h->lossp;
+  a.part = h->xpart;
+  a.r = h->xr;
+  a.g = h->xg;
+  a.lterm = nullptr;
+  a.done = h->xcnt;
+  a.bdone = h->xcnt + pl.nblk;
+  a.rowcnt = h->xcnt + 2 * pl.nblk;
   a.status = h->status;
   a.limit_ns = h->limit_ns;
   return a;
+}
+
+// one fused pass (counters of this plan zeroed first, rowcnt included)
+cudaError_t run_pass(relax_handle* h, const XBPlan& pl, const XBArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(h->xcnt + 2 * pl.nblk, 0, sizeof(unsigned) * (size_t)h->n, st);
+  if (e != cudaSuccess) return e;
+  return xblock_launch(pl, a, st);
 }
 
 PArgs base_pargs(relax_handle* h) {
@@ -255,7 +323,7 @@ PArgs base_pargs(relax_handle* h) {
   a.rho = 2.0 * h->lambda2 / h->L;
   a.eta = h->eta;
   a.max_iters = h->max_iters;
-  a.lossp = h->lossp;
+  a.lossp = nullptr;
   a.acc = h->acc;
   a.bpart = h->bpart;
   a.status = h->status;
@@ -265,39 +333,31 @@ PArgs base_pargs(relax_handle* h) {
 
 // L = c_f * ||X||_2^2 by power iteration on the operator the loop uses
 relax_status power_iteration(relax_handle* h, double* L_out) {
-  const bool dbl = h->dtype == RELAX_F64;
-  void* v = h->vb[0];
-  void* w = h->vb[1];
+  double* v = (double*)h->vb[8];
+  double* w = (double*)h->vb[9];
   const unsigned g = grid_for(h->p);
-  const double v0 = 1.0 / std::sqrt((double)h->p);
-  if (dbl) fill_kernel<double><<<g, 256, 0, h->stream>>>((double*)v, h->p, v0);
-  else fill_kernel<float><<<g, 256, 0, h->stream>>>((float*)v, h->p, (float)v0);
+  fill_kernel<double><<<g, 256, 0, h->stream>>>(v, h->p, 1.0 / std::sqrt((double)h->p));
   CU(cudaGetLastError());
   double ray_prev = 0.0, ray = 0.0;
   for (int it = 0; it < 500; ++it) {
     PassState ps{};
     ps.beta = v;
+    ps.zout = h->vb[10];
     *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;   // staging in pinned memory
     CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-    XPassArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux, h->part_loop);
-    CU(xpass_launch(h->pl_ident, a, h->stream));
-    CU(cudaMemsetAsync(h->dscr, 0, sizeof(double), h->stream));
-    if (dbl)
-      reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>((const double*)h->part_loop, h->pl_ident.ncl, 1,
-                                                                       h->p, (double*)w, h->dscr);
-    else
-      reduce_partials_kernel<float, float><<<g, 256, 0, h->stream>>>((const float*)h->part_loop, h->pl_ident.ncl, 1,
-                                                                     h->p, (float*)w, h->dscr);
+    XBArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux);
+    CU(run_pass(h, h->pl_ident, a, h->stream));
+    CU(cudaMemsetAsync(h->dscr, 0, 2 * sizeof(double), h->stream));
+    reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, 1, 1, h->p, w, h->dscr);
+    sumsq_kernel<<<grid_for(h->n), 256, 0, h->stream>>>((const double*)h->vb[10], h->n, h->dscr + 1);
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(h->h_d, h->lossp, sizeof(double) * 2 * h->pl_ident.ncl, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     int dst = 0;
     CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (dst != ST_OK) return map_dev_status(dst);
-    ray = 0.0;
-    for (int c = 0; c < h->pl_ident.ncl; ++c) ray += h->h_d[2 * c];   // ||X v||^2 with ||v|| = 1
-    if (dbl) scale_kernel<double><<<g, 256, 0, h->stream>>>((double*)w, h->p, h->dscr);
-    else scale_kernel<float><<<g, 256, 0, h->stream>>>((float*)w, h->p, h->dscr);
+    ray = h->h_d[1];   // ||X v||^2 with ||v|| = 1
+    scale_kernel<double><<<g, 256, 0, h->stream>>>(w, h->p, h->dscr);
     CU(cudaGetLastError());
     std::swap(v, w);
     if (it > 3 && std::fabs(ray - ray_prev) <= 1e-7 * ray) break;
@@ -322,28 +382,37 @@ relax_status count_fixings(relax_handle* h, const int8_t* fix, int* j1, int* jf)
   return RELAX_OK;
 }
 
-// FP64 Phi(beta_p), Psi(zeta(beta_d)) with the master X -> h->h_d[0..1]
-relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd) {
+// FP64 Phi(beta_p) and Psi(zeta) with the master X -> h->h_d[0..1].
+// zeta = -grad F(X beta_d) when zd == NULL, else zeta = -grad F(zd) (a dual
+// point given by its z).
+relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd, const void* zd) {
+  const XBPlan& pl = zd ? h->pl_certz : h->pl_cert;
   PassState ps{};
   ps.beta = bp;
-  ps.beta2 = bd;
+  ps.beta2 = zd ? nullptr : bd;
+  ps.zprev = zd;
   *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
   CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-  XPassArgs a = pass_args(h, h->pl_cert, h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI, h->ps_aux,
-                          h->part_cert);
+  const int link = zd ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
+                      : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
+  XBArgs a = pass_args(h, pl, link, h->ps_aux);
   a.X = h->X;
   a.ldx = h->ldx;
   a.colscale = nullptr;
-  CU(xpass_launch(h->pl_cert, a, h->stream));
+  a.lterm = h->lterm;
+  CU(run_pass(h, pl, a, h->stream));
   PArgs pa = base_pargs(h);
   pa.mode = PM_EVAL;
   pa.fix = fix;
-  pa.part = h->part_cert;
-  pa.ncl = h->pl_cert.ncl;
+  pa.part = h->xg;
+  pa.ncl = 1;
   pa.NB = 1;
   pa.st = nullptr;
   pa.vin = bp;
   pa.out = h->dscr;
+  pa.fast_s1 = 0;
+  pa.lossp = h->lterm;
+  pa.n = h->n;
   pa.bar = h->bar_aux;
   pa.bar_base = 0;
   CU(cudaMemsetAsync(h->bar_aux, 0, sizeof(unsigned long long), h->stream));
@@ -356,6 +425,8 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
 }  // namespace
 
 extern "C" {
+
+const char* relax_error_detail(void) { return g_detail; }
 
 const char* relax_strerror(relax_status s) {
   switch (s) {
@@ -394,7 +465,15 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     rs = (x);                           \
     if (rs != RELAX_OK) goto fail;      \
   } while (0)
-#define TRYC(x) TRY(((x) == cudaSuccess) ? RELAX_OK : map_cuda(cudaGetLastError()))
+#define TRYC(x)                                   \
+  do {                                            \
+    cudaError_t ec_ = (x);                        \
+    if (ec_ != cudaSuccess) {                     \
+      set_detail(#x, ec_, __LINE__);              \
+      rs = map_cuda(ec_);                         \
+      goto fail;                                  \
+    }                                             \
+  } while (0)
   {
     cudaGetDevice(&h->dev);
     h->stream = (cudaStream_t)stream;
@@ -424,8 +503,9 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       h->X = h->Xown;
       h->ldx = lda;
     }
-    TRY(alloc(&h->y, (size_t)n * es));
-    TRYC(cudaMemcpyAsync(h->y, y, (size_t)n * es, cudaMemcpyDeviceToDevice, h->stream));
+    TRY(alloc(&h->y, (size_t)n * sizeof(double)));
+    to_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(y, dtype == RELAX_F64 ? 1 : 0, (double*)h->y, n);
+    TRYC(cudaGetLastError());
     // low-precision loop copy of X (BF16 unscaled, FP8 with per-column scales)
     h->xk_loop = dtype == RELAX_F64 ? XK_F64 : XK_F32;
     if (prec == RELAX_BF16 || prec == RELAX_FP8E4M3) {
@@ -453,20 +533,37 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       }
     }
     const bool vd = dtype == RELAX_F64;
-    TRYC(xpass_plan(h->pl_loop, h->xk_loop, vd, false, 1, loss == RELAX_LS ? 1 : 2, n, p));
-    TRYC(xpass_plan(h->pl_ident, h->xk_loop, vd, false, 1, 1, n, p));
-    TRYC(xpass_plan(h->pl_cert, vd ? XK_F64 : XK_F32, vd, true, 2, 1, n, p));
-    TRYC(pphase_plan(h->pp_iter, vd, vd, p));
-    TRYC(pphase_plan(h->pp_eval, vd, true, p));
-    const int ncl_max = std::max(std::max(h->pl_loop.ncl, h->pl_ident.ncl), h->pl_cert.ncl);
-    TRY(alloc(&h->part_loop, (size_t)h->pl_loop.ncl * h->pl_loop.NB * p * es +
-                                 (size_t)h->pl_ident.ncl * p * es));
-    TRY(alloc(&h->part_cert, (size_t)h->pl_cert.ncl * p * sizeof(double)));
-    TRY(alloc((void**)&h->lossp, (size_t)ncl_max * 2 * sizeof(double)));
+    TRYC(xblock_plan(h->pl_loop, h->xk_loop, false, 1, loss == RELAX_LS ? 1 : 2, n, p));
+    TRYC(xblock_plan(h->pl_ident, h->xk_loop, false, 1, 1, n, p));
+    TRYC(xblock_plan(h->pl_cert, vd ? XK_F64 : XK_F32, true, 2, 1, n, p));
+    TRYC(xblock_plan(h->pl_certz, vd ? XK_F64 : XK_F32, true, 1, 1, n, p));
+    if (std::getenv("RELAX_DEBUG")) {
+      const XBPlan& q = h->pl_loop;
+      std::fprintf(stderr, "[relax] loop pass: xk=%d B=%d nblk=%d lag=%d nchunk=%d cw=%lld sw=%lld grid=%d smem=%zu beta_smem=%d\n",
+                   q.xk, q.B, q.nblk, q.lag, q.nchunk, (long long)q.cw, (long long)q.sw, q.grid, q.smem, q.beta_smem);
+    }
+    TRYC(pphase_plan(h->pp_iter, true, p));
+    TRYC(pphase_plan(h->pp_eval, true, p));
+    {
+      const XBPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
+      size_t part_n = 0;
+      int nblk_max = 0;
+      for (const XBPlan* q : pls) {
+        part_n = std::max(part_n, (size_t)n * q->nchunk * q->NF);
+        nblk_max = std::max(nblk_max, q->nblk);
+      }
+      TRY(alloc((void**)&h->xpart, part_n * sizeof(double)));
+      TRY(alloc((void**)&h->xr, (size_t)2 * n * sizeof(double)));
+      TRY(alloc((void**)&h->xg, (size_t)2 * p * sizeof(double)));
+      TRY(alloc((void**)&h->lterm, (size_t)2 * n * sizeof(double)));
+      TRY(alloc((void**)&h->xcnt, ((size_t)2 * nblk_max + n) * sizeof(unsigned)));
+    }
     TRY(alloc((void**)&h->st, sizeof(IterState)));
     TRY(alloc((void**)&h->ps_aux, sizeof(PassState)));
-    for (int i = 0; i < 6; ++i) TRY(alloc(&h->vb[i], (size_t)p * es));
-    for (int i = 6; i < 8; ++i) TRY(alloc(&h->vb[i], (size_t)n * es));
+    for (int i = 0; i < 6; ++i) TRY(alloc(&h->vb[i], (size_t)p * sizeof(double)));
+    for (int i = 6; i < 8; ++i) TRY(alloc(&h->vb[i], (size_t)n * sizeof(double)));
+    for (int i = 8; i < 10; ++i) TRY(alloc(&h->vb[i], (size_t)p * sizeof(double)));
+    for (int i = 10; i < 13; ++i) TRY(alloc(&h->vb[i], (size_t)n * sizeof(double)));
     TRY(alloc((void**)&h->acc, 3 * ACC_STRIDE * sizeof(unsigned long long)));
     const int gmax = std::max(h->pp_iter.grid, h->pp_eval.grid);
     TRY(alloc((void**)&h->bpart, (size_t)2 * gmax * NBP * sizeof(double)));
@@ -477,7 +574,6 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRY(alloc((void**)&h->iscr, 16 * sizeof(int)));
     TRYC(cudaMemsetAsync(h->acc, 0, 3 * ACC_STRIDE * sizeof(unsigned long long), h->stream));
     TRYC(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
-    TRYC(cudaMemsetAsync(h->lossp, 0, (size_t)ncl_max * 2 * sizeof(double), h->stream));
     TRYC(cudaHostAlloc((void**)&h->h_state, sizeof(IterState), cudaHostAllocDefault));
     TRYC(cudaHostAlloc((void**)&h->h_done, 2 * sizeof(int), cudaHostAllocDefault));
     TRYC(cudaHostAlloc((void**)&h->h_d, 1024 * sizeof(double), cudaHostAllocDefault));
@@ -509,22 +605,13 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   relax_status rs = count_fixings(h, fixings, &j1, &jf);
   if (rs != RELAX_OK) return rs;
   if (h->k < j1) return RELAX_EINVAL;
-  const bool dbl = h->dtype == RELAX_F64;
-  const size_t es = h->esz();
   std::memset(out, 0, sizeof(*out));
   out->lipschitz = h->L;
-  // ---- state
+  // ---- state (loop vectors are FP64)
   const unsigned g = grid_for(std::max(h->p, h->n));
-  if (dbl)
-    init_vectors_kernel<double><<<g, 256, 0, h->stream>>>((const double*)warm_start, (double*)h->vb[0],
-                                                          (double*)h->vb[1], (double*)h->vb[4], (double*)h->vb[5],
-                                                          (double*)h->vb[2], (double*)h->vb[3], h->p,
-                                                          (double*)h->vb[6], (double*)h->vb[7], h->n);
-  else
-    init_vectors_kernel<float><<<g, 256, 0, h->stream>>>((const float*)warm_start, (float*)h->vb[0],
-                                                         (float*)h->vb[1], (float*)h->vb[4], (float*)h->vb[5],
-                                                         (float*)h->vb[2], (float*)h->vb[3], h->p, (float*)h->vb[6],
-                                                         (float*)h->vb[7], h->n);
+  init_vectors_kernel<<<g, 256, 0, h->stream>>>(warm_start, h->f64(), (double*)h->vb[0], (double*)h->vb[1],
+                                                (double*)h->vb[4], (double*)h->vb[5], (double*)h->vb[2],
+                                                (double*)h->vb[3], h->p, (double*)h->vb[6], (double*)h->vb[7], h->n);
   CU(cudaGetLastError());
   IterState s{};
   s.beta_prev = h->vb[0];
@@ -533,6 +620,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.G_cur = h->vb[3];
   s.beta_best = h->vb[4];
   s.beta_dbest = h->vb[5];
+  s.z_dbest = h->vb[12];
   s.z_prev = h->vb[6];
   s.z_cur = h->vb[7];
   s.tau = 1.0;
@@ -541,8 +629,9 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.psi_best = -INFINITY;
   s.kbar = h->k - j1;
   s.pbar = jf;
+  s.tol = gap_tol;
   s.ps.beta = s.beta_cur;
-  s.ps.zout = h->loss == RELAX_LOGISTIC ? s.z_cur : nullptr;
+  s.ps.zout = s.z_cur;
   s.ps.zprev = s.z_prev;
   s.ps.mom = 0.0;
   *h->h_state = s;
@@ -550,16 +639,20 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
   // ---- one iteration = fused X-pass + p-phase; enqueue `chunk` per host poll
-  XPassArgs xa = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps, h->part_loop);
+  XBArgs xa = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps);
   PArgs pa = base_pargs(h);
   pa.mode = PM_ITER;
   pa.fix = fixings;
-  pa.part = h->part_loop;
-  pa.ncl = h->pl_loop.ncl;
+  pa.part = h->xg;
+  pa.ncl = 1;
   pa.NB = h->pl_loop.NB;
   pa.st = h->st;
   pa.bar = h->bar;
   pa.tol = gap_tol;
+  pa.fast_s1 = h->dtype == RELAX_F32 ? 1 : 0;   // FP32-key top-k select only for FP32 data
+  pa.lossp = nullptr;                          // loss terms from z^t (FP64, in the p-phase)
+  pa.y = (const double*)h->y;
+  pa.n = h->n;
   // Timing mode: event records around every loop kernel (captured into the
   // graph); the host then waits for each chunk before enqueueing the next.
   const bool timing = h->opt.timing != 0;
@@ -573,11 +666,11 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   auto enqueue_body = [&](cudaStream_t cs) -> cudaError_t {
     for (int i = 0; i < chunk; ++i) {
       cudaError_t e;
-      if (timing && (e = cudaEventRecord(tev[3 * i], cs)) != cudaSuccess) return e;
-      if ((e = xpass_launch(h->pl_loop, xa, cs)) != cudaSuccess) return e;
-      if (timing && (e = cudaEventRecord(tev[3 * i + 1], cs)) != cudaSuccess) return e;
+      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      if ((e = run_pass(h, h->pl_loop, xa, cs)) != cudaSuccess) return e;
+      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
       if ((e = pphase_launch(h->pp_iter, pa, cs)) != cudaSuccess) return e;
-      if (timing && (e = cudaEventRecord(tev[3 * i + 2], cs)) != cudaSuccess) return e;
+      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 2], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
@@ -607,29 +700,76 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   const int64_t max_chunks = (int64_t)h->max_iters / chunk + 3;
   cudaError_t err = cudaSuccess;
   int64_t nchunks = 0;
-  std::vector<float> xms, pms;   // per launched iteration (timing mode)
-  for (int64_t c = 0; c < max_chunks; ++c) {
-    err = enqueue_chunk();
-    if (err != cudaSuccess) break;
-    ++nchunks;
-    cudaMemcpyAsync(&h->h_done[c & 1], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    cudaEventRecord(ev[c & 1], h->stream);
-    if (timing) {
-      cudaEventSynchronize(ev[c & 1]);
-      for (int i = 0; i < chunk; ++i) {
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, tev[3 * i], tev[3 * i + 1]);
-        cudaEventElapsedTime(&b, tev[3 * i + 1], tev[3 * i + 2]);
-        xms.push_back(a);
-        pms.push_back(b);
+  std::vector<float> xms, pms;   // per launched iteration of the current run (timing mode)
+  double xms_work = 0.0, pms_work = 0.0;
+  int passes_work = 0;
+  auto run_loop = [&]() {
+    xms.clear();
+    pms.clear();
+    for (int64_t c = 0; c < max_chunks; ++c) {
+      err = enqueue_chunk();
+      if (err != cudaSuccess) break;
+      ++nchunks;
+      cudaMemcpyAsync(&h->h_done[c & 1], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+      cudaEventRecord(ev[c & 1], h->stream);
+      if (timing) {
+        cudaEventSynchronize(ev[c & 1]);
+        for (int i = 0; i < chunk; ++i) {
+          float a = 0.f, b = 0.f;
+          cudaEventElapsedTime(&a, tev[3 * i], tev[3 * i + 1]);
+          cudaEventElapsedTime(&b, tev[3 * i + 1], tev[3 * i + 2]);
+          xms.push_back(a);
+          pms.push_back(b);
+        }
+        if (h->h_done[c & 1]) break;
+      } else if (c >= 1) {
+        cudaEventSynchronize(ev[(c - 1) & 1]);
+        if (h->h_done[(c - 1) & 1]) break;
       }
-      if (h->h_done[c & 1]) break;
-    } else if (c >= 1) {
-      cudaEventSynchronize(ev[(c - 1) & 1]);
-      if (h->h_done[(c - 1) & 1]) break;
     }
+    cudaStreamSynchronize(h->stream);
+  };
+  // the first iters_in_run + 1 launches of a run did work; the rest of its last
+  // chunk returned at once
+  auto account = [&](int it_before, int it_after) {
+    const int work = std::min<int>((int)xms.size(), it_after - it_before + 1);
+    for (int t = 0; t < work; ++t) { xms_work += xms[t]; pms_work += pms[t]; }
+    passes_work += it_after - it_before + 1;
+  };
+  int it_before = 0;
+  run_loop();
+  // The loop's gap is tracked in the working precision; when the FP64
+  // certificate of the final pair misses gap_tol, continue with a tighter
+  // internal tolerance (at most 3 times).
+  int cert_rounds = 0;
+  double cert_primal = 0.0, cert_dual = 0.0;
+  bool have_cert = false;
+  for (;;) {
+    if (err != cudaSuccess) break;
+    CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
+    int dst0 = 0;
+    CU(cudaMemcpy(&dst0, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    account(it_before, h->h_state->iter);
+    if (dst0 != ST_OK || !h->certify) break;
+    const IterState& S0 = *h->h_state;
+    rs = certify(h, fixings, S0.beta_best, nullptr, S0.z_dbest);
+    if (rs != RELAX_OK) return rs;
+    out->launches += 2;
+    have_cert = true;
+    cert_primal = h->h_d[0];
+    cert_dual = h->h_d[1];
+    const double crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
+    if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel)) break;
+    ++cert_rounds;
+    double tol_new = S0.tol * 0.25;
+    int zero = 0;
+    CU(cudaMemcpyAsync(&h->st->tol, &tol_new, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(&h->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(&h->st->ps.done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    it_before = S0.iter;
+    run_loop();
   }
-  cudaStreamSynchronize(h->stream);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (tev) {
@@ -638,50 +778,38 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   if (err != cudaSuccess) return map_cuda(err);
-  out->launches = (int)(nchunks * chunk * 2) + 1 + (fixings ? 1 : 0);   // loop + init (+ count)
+  out->launches += (int)(nchunks * chunk * 2) + 1 + (fixings ? 1 : 0);   // loop + init (+ count)
   CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
   int dst = 0;
   CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
   const IterState& S = *h->h_state;
   out->iters = S.iter;
-  out->xpass_count = S.iter + 1;
+  out->xpass_count = passes_work;
   if (timing) {
-    // the pass at beta^t and the p-phase that follows it, for t = 0..iters
-    for (int t = 0; t <= S.iter && t < (int)xms.size(); ++t) {
-      out->xpass_ms += xms[t];
-      out->pphase_ms += pms[t];
-    }
+    out->xpass_ms = xms_work;
+    out->pphase_ms = pms_work;
   }
   out->restarts = S.restarts;
   out->primal_loop = S.phi_best;
   out->dual_loop = S.psi_best;
-  out->primal = S.phi_best;
-  out->dual_bound = S.psi_best;
+  out->primal = have_cert ? cert_primal : S.phi_best;
+  out->dual_bound = have_cert ? cert_dual : S.psi_best;
   relax_status status = map_dev_status(dst);
-  if (status == RELAX_OK && h->certify) {
-    rs = certify(h, fixings, S.beta_best, S.beta_dbest);
-    if (rs != RELAX_OK) return rs;
-    out->launches += 2;
-    CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
-    status = map_dev_status(dst);
-    out->primal = h->h_d[0];
-    out->dual_bound = h->h_d[1];
-  }
   out->gap = out->primal - out->dual_bound;
   out->rel_gap = out->gap / std::max(1.0, std::fabs(out->primal));
-  CU(cudaMemcpyAsync(beta_out, S.beta_best, (size_t)h->p * es, cudaMemcpyDeviceToDevice, h->stream));
+  from_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>((const double*)S.beta_best, beta_out, h->f64(), h->p);
+  CU(cudaGetLastError());
   CU(cudaMemsetAsync(h->iscr, 0, sizeof(int), h->stream));
-  if (dbl) nnz_kernel<double><<<grid_for(h->p), 256, 0, h->stream>>>((const double*)S.beta_best, h->p, h->iscr);
-  else nnz_kernel<float><<<grid_for(h->p), 256, 0, h->stream>>>((const float*)S.beta_best, h->p, h->iscr);
+  nnz_kernel<<<grid_for(h->p), 256, 0, h->stream>>>((const double*)S.beta_best, h->p, h->iscr);
   CU(cudaMemcpyAsync(h->h_i, h->iscr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   out->n_nz = h->h_i[0];
-  out->launches += 1;
+  out->launches += 2;
   if (status == RELAX_OK) {
     if (!std::isfinite(out->dual_bound) || std::isnan(out->primal)) status = RELAX_ENUMERIC;
     else if (out->dual_bound > out->primal + 1e-9 * std::max(1.0, std::fabs(out->primal)))
       status = RELAX_EINVALID_BOUND;
-    else if (!(S.phi_best - S.psi_best <= gap_tol * std::max(1.0, std::fabs(S.phi_best))))
+    else if (!(out->rel_gap <= gap_tol))   // the certified gap when certification ran
       status = RELAX_ENOTCONV;
   }
   out->status = status;
@@ -691,34 +819,37 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
 relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g_out, double* loss_host) {
   if (!h || !beta || !g_out) return RELAX_EINVAL;
   CU(cudaSetDevice(h->dev));
+  double* b64 = (double*)h->vb[8];
+  double* g64 = (double*)h->vb[9];
+  double* z64 = (double*)h->vb[10];
+  double* zp64 = (double*)h->vb[11];
+  to_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>(beta, h->f64(), b64, h->p);
+  CU(cudaGetLastError());
   PassState ps{};
-  ps.beta = beta;
-  ps.zout = z_out;
-  ps.zprev = h->vb[6];
+  ps.beta = b64;
+  ps.zout = z64;
+  ps.zprev = zp64;
   ps.mom = 0.0;
   *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
   CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
-  CU(cudaMemsetAsync(h->vb[6], 0, (size_t)h->n * h->esz(), h->stream));
-  XPassArgs a = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, h->ps_aux, h->part_loop);
-  CU(xpass_launch(h->pl_loop, a, h->stream));
+  CU(cudaMemsetAsync(zp64, 0, (size_t)h->n * sizeof(double), h->stream));
+  XBArgs a = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, h->ps_aux);
+  CU(run_pass(h, h->pl_loop, a, h->stream));
   const unsigned g = grid_for(h->p);
-  if (h->dtype == RELAX_F64)
-    reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>((const double*)h->part_loop, h->pl_loop.ncl,
-                                                                     h->pl_loop.NB, h->p, (double*)g_out, nullptr);
-  else
-    reduce_partials_kernel<float, float><<<g, 256, 0, h->stream>>>((const float*)h->part_loop, h->pl_loop.ncl,
-                                                                   h->pl_loop.NB, h->p, (float*)g_out, nullptr);
+  reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, 1, h->pl_loop.NB, h->p, g64, nullptr);
+  from_f64_kernel<<<g, 256, 0, h->stream>>>(g64, g_out, h->f64(), h->p);
+  if (z_out) from_f64_kernel<<<grid_for(h->n), 256, 0, h->stream>>>(z64, z_out, h->f64(), h->n);
+  CU(cudaMemsetAsync(h->dscr, 0, 2 * sizeof(double), h->stream));
+  loss_terms_kernel<<<grid_for(h->n), 256, 0, h->stream>>>(z64, (const double*)h->y, h->n, h->loss, h->dscr);
   CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(h->h_d, h->lossp, sizeof(double) * 2 * h->pl_loop.ncl, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   int dst = 0;
   CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (loss_host) {
-    double f = 0.0, d = 0.0;
-    for (int c = 0; c < h->pl_loop.ncl; ++c) { f += h->h_d[2 * c]; d += h->h_d[2 * c + 1]; }
-    loss_host[0] = f;
-    loss_host[1] = d;
+    loss_host[0] = h->h_d[0];
+    loss_host[1] = h->h_d[1];
   }
   return map_dev_status(dst);
 }
@@ -732,7 +863,10 @@ relax_status relax_certify(relax_handle* h, const int8_t* fixings, const void* b
   if (rs != RELAX_OK) return rs;
   if (h->k < j1) return RELAX_EINVAL;
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
-  rs = certify(h, fixings, beta_primal, beta_dual);
+  to_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>(beta_primal, h->f64(), (double*)h->vb[8], h->p);
+  to_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>(beta_dual, h->f64(), (double*)h->vb[9], h->p);
+  CU(cudaGetLastError());
+  rs = certify(h, fixings, h->vb[8], h->vb[9], nullptr);
   if (rs != RELAX_OK) return rs;
   int dst = 0;
   CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -748,7 +882,7 @@ static relax_status standalone(int mode, const void* vin, void* vout, int64_t p,
   if (!vin || p <= 0 || k < 0 || !(M > 0.0) || (dtype != RELAX_F64 && dtype != RELAX_F32)) return RELAX_EINVAL;
   const bool dbl = dtype == RELAX_F64;
   PPlan pl;
-  CU(pphase_plan(pl, dbl, dbl, p));
+  CU(pphase_plan(pl, dbl, p));
   // scratch: round accumulators, block partials, barrier counter, status, output
   const size_t acc_b = 3 * ACC_STRIDE * sizeof(unsigned long long);
   const size_t bp_b = (size_t)2 * pl.grid * NBP * sizeof(double);

@@ -1,8 +1,9 @@
-// Host-side launch plans for the fused X-pass and the p-phase.
+// Host-side launch plans for the fused pass over X and the p-phase.
 #pragma once
 #include <cuda_runtime.h>
 
 #include "pphase.cuh"
+#include "xblock.cuh"
 #include "xpass.cuh"
 
 namespace relax {
@@ -13,33 +14,30 @@ enum XKind : int { XK_F64 = 0, XK_F32 = 1, XK_BF16 = 2, XK_FP8 = 3 };
 inline int xkind_esize(int xk) { return xk == XK_F64 ? 8 : xk == XK_F32 ? 4 : xk == XK_BF16 ? 2 : 1; }
 inline int xkind_vec(int xk) { return 16 / xkind_esize(xk); }
 
-struct XPlan {
-  int xk = 0;           // storage of X
-  bool vec_double = false;  // beta / y / partial storage is double (X in F64)
-  bool cert = false;    // FP64 accumulation, 2 forward vectors
+// Fused pass by L2 row blocking (xblock.cuh)
+struct XBPlan {
+  int xk = 0;
+  bool cert = false;       // FP64 accumulation (certification / power iteration of FP64 data)
   int NF = 1, NB = 1;
-  int NV = 2, R = 2, S = 2, C = 1;
-  int64_t slice = 0;
-  uint32_t slot_bytes = 0;
+  int64_t cw = 0;          // chunk columns
+  int nchunk = 1;
+  int B = 1, nblk = 1, lag = 2;
+  int64_t sw = 0;          // strip columns per CTA
+  int beta_smem = 0;
+  int grid = 1;
   size_t smem = 0;
-  int ncl = 1;          // clusters launched
   const void* kernel = nullptr;
 };
-
-constexpr int XBLOCK = 224;  // consumer threads (7 warps) + 1 producer warp = 256
-
-// Builds a plan (chooses NV, C, R, S; queries cluster occupancy).  Returns
-// cudaErrorNotSupported when p is too large for one cluster of <= 16 CTAs.
-cudaError_t xpass_plan(XPlan& pl, int xk, bool vec_double, bool cert, int NF, int NB, int64_t n,
-                       int64_t p);
-cudaError_t xpass_launch(const XPlan& pl, const XPassArgs& a, cudaStream_t st);
+cudaError_t xblock_plan(XBPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p);
+// counters (2 * nblk unsigned) are zeroed on the stream before the launch
+cudaError_t xblock_launch(const XBPlan& pl, const XBArgs& a, cudaStream_t st);
 
 struct PPlan {
   const void* kernel = nullptr;
   int grid = 1;
-  bool vdouble = false, gdouble = false;
+  bool vdouble = false;
 };
-cudaError_t pphase_plan(PPlan& pl, bool vdouble, bool gdouble, int64_t p);
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p);
 cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st);
 
 }  // namespace relax

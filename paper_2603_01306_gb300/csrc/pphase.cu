@@ -5,14 +5,11 @@
 
 namespace relax {
 
-cudaError_t pphase_plan(PPlan& pl, bool vdouble, bool gdouble, int64_t p) {
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p) {
   pl = PPlan{};
   pl.vdouble = vdouble;
-  pl.gdouble = gdouble;
-  if (vdouble && gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<double, double>);
-  else if (!vdouble && gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<float, double>);
-  else if (!vdouble && !gdouble) pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<float, float>);
-  else return cudaErrorNotSupported;
+  pl.kernel = vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double>)
+                      : reinterpret_cast<const void*>(&pphase_kernel<float>);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

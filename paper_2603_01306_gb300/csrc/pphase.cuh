@@ -2,8 +2,12 @@
 //
 //   P0  G^t = sum of the per-cluster X'r partials; a = -G^t/(2 lambda2) (the
 //       argument of g* in Psi, since X'zeta = -G^t); |beta^t| statistics.
-//   S1  TopSum_{kbar} H_M(|a_Jf|) of Lemma 4.2: exact kbar-th largest |a| by a
-//       radix select over the key bits (32 candidates per round, one per lane).
+//   S1  TopSum_{kbar} H_M(|a_Jf|) of Lemma 4.2 through its variational form
+//       TopSum_k(h) = min_t k t + sum_j (h_j - t)_+ at t = the kbar-th largest h,
+//       found by a radix select over key bits (32 candidates per round, one per
+//       lane).  The certification and the standalone g* use the exact keys of
+//       the values; the loop selects on FP32-rounded keys, which makes the sum an
+//       upper bound within FP32 rounding (Psi stays a valid bound).
 //   S2  g_N(beta^t) (Thm 4.4 / Algorithm 1): the water level w of Algorithm 1
 //       is the root of sum_j min(|beta_j|, w) = kbar w; a multisection over the
 //       bits of w brackets it, an exact FP64 closed-form step finishes it:
@@ -23,6 +27,8 @@
 //          c = (S_mid - M (kbar - N_top)) / N_mid              (c >  rho M)
 //   P2  beta^{t+1}.
 //
+// Multisection rounds evaluate FP32-rounded values; every decision that fixes
+// an output (classification against a threshold, closed forms, sums) is FP64.
 // Grid-wide steps use a bounded barrier (the grid is co-resident: cooperative
 // launch sized by occupancy).  Round counters are exact integer atomics (the
 // z-sums in 32.32 fixed point), so every block takes identical decisions; FP64
@@ -39,7 +45,7 @@ constexpr int PNW = PBLOCK / 32;
 constexpr int PEPT = 4;         // max elements per thread
 constexpr int NFIELD = 8;       // round accumulator fields
 constexpr int ACC_STRIDE = NFIELD * PQ;
-constexpr int NBP = 8;          // doubles per block partial
+constexpr int NBP = 10;         // doubles per block partial
 constexpr int MAX_POLISH = 8;
 
 enum PMode : int { PM_ITER = 0, PM_EVAL = 1, PM_PROX = 2, PM_GVAL = 3, PM_GSTAR = 4 };
@@ -57,10 +63,12 @@ struct IterState {
   void* z_cur;
   void* beta_best;              // argmin Phi so far
   void* beta_dbest;             // beta whose induced zeta gave max Psi
+  void* z_dbest;                // z^t = X beta^t of that iterate (its dual point zeta = -grad F(z))
   double tau;                   // FISTA t_k
   double gap_ref;               // gap at the start of the current restart epoch
   double phi_best, psi_best;
   double phi_t, psi_t, g_t, c_last;
+  double tol;                   // stop when (Phi_best - Psi_best) <= tol * max(1, |Phi_best|)
   int iter, restarts, have_ref, done, kbar, pbar, n_nz, n_top;
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
@@ -73,14 +81,17 @@ struct PArgs {
   double lambda2, M, step, rho, eta, tol;
   int max_iters;
   const int8_t* fix;            // NULL = root
-  const void* part;             // [ncl][NB][p] (ITER: TG=TV; EVAL: double)
+  const void* part;             // [ncl][NB][p] doubles
   int ncl, NB;
-  const double* lossp;          // [ncl][2]
+  const double* lossp;          // [n][2] per-row loss terms (certification); NULL: from z and y
+  const double* y;              // n: response (loss terms from z^t in the loop)
+  int64_t n;
   IterState* st;
   const void* vin;              // PROX: v; GVAL: beta; GSTAR: alpha; EVAL: beta_primal
   void* vout;                   // PROX output
   int* counts;                  // PROX: {n_top, n_nz}
   double* out;                  // EVAL: {Phi, Psi}; GVAL: g; GSTAR: g*
+  int fast_s1;                  // select the kbar-th largest |a| on FP32 keys (loop)
   unsigned long long* acc;      // [3][ACC_STRIDE], zero between launches
   double* bpart;                // [2][gridDim][NBP]
   unsigned long long* bar;      // grid barrier counter
@@ -109,10 +120,12 @@ __device__ __forceinline__ unsigned long long fixp(double z) {
   return __double2ull_rz(z * 4294967296.0);
 }
 
-template <typename TV, typename TG>
+// TV: element type of the p-vectors (double in the loop and certification;
+// float or double for the standalone entry points).
+template <typename TV>
 __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
-  using KG = typename KeyOf<TG>::type;   // keys of |a| (S1)
-  using KV = typename KeyOf<TV>::type;   // keys of |beta| (S2) and of c (S3)
+  using KG = unsigned long long;   // S1 keys: FP32 or FP64 bit patterns of |a|
+  using KV = uint32_t;             // FP32 keys of the S2 / S3 thresholds
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = gridDim.x * PBLOCK;
   const int gt = blockIdx.x * PBLOCK + tid;
@@ -153,11 +166,11 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       bp[(size_t)blockIdx.x * NBP + tid] = s;
     }
     barrier();
-    if (warp < nv) {
+    for (int c = warp; c < nv; c += PNW) {
       double s = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(bp + (size_t)b * NBP + warp);
+      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(bp + (size_t)b * NBP + c);
       s = warp_sum(s);
-      if (lane == 0) sh_tot[warp] = s;
+      if (lane == 0) sh_tot[c] = s;
     }
     __syncthreads();
     for (int i = 0; i < nv; ++i) v[i] = sh_tot[i];
@@ -192,42 +205,66 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   // ---------------------------------------------------------------- P0
   const TV* bcur = nullptr;
   const TV* bprev = nullptr;
-  const TG* Gprev = nullptr;
-  TG* Gcur = nullptr;
+  const double* Gprev = nullptr;
+  double* Gcur = nullptr;
   if (mode == PM_ITER) {
     bcur = static_cast<const TV*>(st->beta_cur);
     bprev = static_cast<const TV*>(st->beta_prev);
-    Gprev = static_cast<const TG*>(st->G_prev);
-    Gcur = static_cast<TG*>(st->G_cur);
+    Gprev = static_cast<const double*>(st->G_prev);
+    Gcur = static_cast<double*>(st->G_cur);
   } else if (mode == PM_EVAL || mode == PM_GVAL) {
     bcur = static_cast<const TV*>(a.vin);
   }
-  const TG* part = static_cast<const TG*>(a.part);
+  const double* part = static_cast<const double*>(a.part);
+  // S1 keys: FP64 patterns when the values are FP64 and exactness is asked for
+  const bool key64 = !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
 
   int8_t fx[PEPT];
   KG ka[PEPT];        // S1 keys: |a| on Jf, 0 elsewhere
   TV bm[PEPT];        // S2: |beta| on Jf, 0 elsewhere
+  float bmf[PEPT];    // the same, rounded to FP32 for the multisection rounds
   TV bt[PEPT];        // beta^t
-  TG gg[PEPT];        // G^t
-  TG gy[PEPT];        // logistic: X' grad F at the tentative y^t
+  double gg[PEPT];    // G^t
+  double gy[PEPT];    // logistic: X' grad F at the tentative y^t
   // sums: 0 sum_J1 H(a), 1 sum_J1 b^2, 2 sum_Jf |b|, 3 sum_Jf b^2, 4 nnz_Jf(b),
-  //       5 domain violations, 6 non-finite, 7 sum_Jf H(a)
-  double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
+  //       5 domain violations, 6 non-finite, 7 sum_Jf H(a), 8 F(z), 9 -F*(-zeta)
+  double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (a.lossp) {
+    // per-row loss terms written by the certification pass
+    for (int64_t i = gt; i < a.n; i += nthr) {
+      s0[8] += a.lossp[2 * i];
+      s0[9] += a.lossp[2 * i + 1];
+    }
+  } else if (mode == PM_ITER) {
+    // loss terms of Eq. 6-7 at z^t = X beta^t, zeta = -grad F(z^t), in FP64
+    const double* zt = static_cast<const double*>(st->z_cur);
+    for (int64_t i = gt; i < a.n; i += nthr) {
+      const double yi = a.y[i], zi = zt[i];
+      if (a.loss == 0) {
+        const double d = zi - yi, zeta = -2.0 * d;
+        s0[8] += d * d;
+        s0[9] += zeta * yi - 0.25 * zeta * zeta;
+      } else {
+        s0[8] += softplus_neg(yi * zi);
+        s0[9] += entropy_of(yi * zi);
+      }
+    }
+  }
   const bool need_a = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GSTAR);
   const bool need_b = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GVAL);
 #pragma unroll
   for (int e = 0; e < PEPT; ++e) {
     const int64_t j = (int64_t)gt + (int64_t)e * nthr;
-    fx[e] = 0; ka[e] = 0; bm[e] = (TV)0; bt[e] = (TV)0; gg[e] = (TG)0; gy[e] = (TG)0;
+    fx[e] = 0; ka[e] = 0; bm[e] = (TV)0; bmf[e] = 0.f; bt[e] = (TV)0; gg[e] = 0.0; gy[e] = 0.0;
     if (j >= p) { fx[e] = -2; continue; }
     const int8_t f = a.fix ? a.fix[j] : (int8_t)0;
     fx[e] = f;
     if (need_a) {
-      TG av;
+      double av;
       if (mode == PM_GSTAR) {
-        av = static_cast<const TG*>(a.vin)[j];
+        av = (double)static_cast<const TV*>(a.vin)[j];
       } else {
-        TG G = (TG)0, Gy = (TG)0;
+        double G = 0.0, Gy = 0.0;   // cluster partials summed in FP64, fixed order
         for (int c = 0; c < a.ncl; ++c) {
           G += part[((int64_t)c * a.NB) * p + j];
           if (a.NB > 1) Gy += part[((int64_t)c * a.NB + 1) * p + j];
@@ -235,12 +272,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
         gg[e] = G;
         gy[e] = Gy;
         if (mode == PM_ITER) Gcur[j] = G;
-        av = -G / (TG)(2.0 * lam2);
+        av = -G / (2.0 * lam2);
       }
-      if (!isfinite((double)av)) s0[6] += 1.0;
-      const TG aa = av < (TG)0 ? -av : av;
-      if (f > 0) s0[0] += (double)huber_d<TG>(aa, (TG)M);
-      if (f == 0) { ka[e] = key_of(aa); s0[7] += (double)huber_d<TG>(aa, (TG)M); }
+      if (!isfinite(av)) s0[6] += 1.0;
+      const double aa = fabs(av);
+      if (f > 0) s0[0] += huber_d<double>(aa, M);
+      if (f == 0) {
+        ka[e] = key64 ? (KG)key_of(aa) : (KG)key_of((float)aa);
+        s0[7] += huber_d<double>(aa, M);
+      }
     }
     if (need_b) {
       const TV b = bcur[j];
@@ -251,6 +291,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       else if (f < 0) { if (b != (TV)0) s0[5] += 1.0; }
       else {
         bm[e] = ab;
+        bmf[e] = (float)ab;
         s0[2] += (double)ab;
         s0[3] += (double)ab * (double)ab;
         if (ab > (TV)0) s0[4] += 1.0;
@@ -277,23 +318,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     pb = (int)cnt2[1];
   }
   (void)kbar;
-  const double Ftot = [&]() {
-    double s = 0.0;
-    if (a.lossp) for (int c = 0; c < a.ncl; ++c) s += a.lossp[c * 2 + 0];
-    return s;
-  }();
-  const double Dtot = [&]() {
-    double s = 0.0;
-    if (a.lossp) for (int c = 0; c < a.ncl; ++c) s += a.lossp[c * 2 + 1];
-    return s;
-  }();
+  const double Ftot = tot[8];
+  const double Dtot = tot[9];
   const bool nonfinite = tot[6] > 0.0;
 
   // ------------------------------------------------------ S1 / S2 setup
   bool s1 = false, s2 = false;
   double topsum = 0.0, gval = 0.0;
-  KG lo1 = 0, hi1 = (KG)(KeyOf<TG>::kInf + 1);
-  KV lo2 = 0, hi2 = (KV)KeyOf<TV>::kInf;
+  KG lo1 = 0, hi1 = key64 ? (KG)(KeyOf<double>::kInf + 1) : (KG)(KeyOf<float>::kInf + 1);
+  KV lo2 = 0, hi2 = (KV)KeyOf<float>::kInf;
   double c2lo = 0.0, c2hi = 0.0;   // #{|b| > lo2}, #{|b| > hi2}
   if (need_a) {
     if (kb <= 0) topsum = 0.0;
@@ -317,8 +350,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
     const KG x1 = s1 ? cand<KG>(lo1, hi1, lane) : (KG)0;
     const KV x2 = s2 ? cand<KV>(lo2, hi2, lane) : (KV)0;
-    const TV w2 = from_key(x2, (TV)0);
-    const TV inv2 = s2 ? (TV)1 / w2 : (TV)0;
+    const float w2 = from_key(x2, 0.f);
+    const float inv2 = s2 ? 1.0f / w2 : 0.f;
     for (int src = 0; src < 32; ++src) {
 #pragma unroll
       for (int e = 0; e < PEPT; ++e) {
@@ -327,10 +360,10 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
           fld[F_S1] += (kv >= x1) ? 1ull : 0ull;
         }
         if (s2) {
-          const TV b = __shfl_sync(0xffffffffu, bm[e], src);
-          if (b > (TV)0) {
-            const TV z = b * inv2;
-            fld[F_S2Z] += fixp(z < (TV)1 ? z : (TV)1);
+          const float b = __shfl_sync(0xffffffffu, bmf[e], src);
+          if (b > 0.f) {
+            const float z = b * inv2;
+            fld[F_S2Z] += fixp(z < 1.f ? z : 1.f);
             fld[F_S2C] += (b > w2) ? 1ull : 0ull;
           }
         }
@@ -364,47 +397,60 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   }
 
   // ---------------------------------------------- exact S1 / S2 finishing
-  // S1: t* = the kbar-th largest |a| (key lo1); TopSum = sum_{|a|>t*} H + (kbar - N_>) H(t*)
-  // S2: w on the bracket's piece; polished until the classification is stable.
+  // S1: t* = the kbar-th largest |a| (key lo1); TopSum = kbar H(t*) + sum (H(|a|) - H(t*))_+
+  // S2: w on the bracket's piece, polished until the classification is stable.
   const bool fin1 = need_a && kb > 0 && pb > kb;
+  const double tstar = fin1 ? (key64 ? from_key((unsigned long long)lo1, 0.0)
+                                     : (double)from_key((uint32_t)lo1, 0.f)) : 0.0;
+  const double htstar = huber_d<double>(tstar, M);
   bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb;
-  double wcur = pol2 ? (double)from_key(hi2, (TV)0) : 0.0;
+  double wcur = pol2 ? (double)from_key(hi2, 0.f) : 0.0;
   double nprev = -1.0;
-  const double wlo = (double)from_key(lo2, (TV)0), whi = (double)from_key(hi2, (TV)0);
+  const double wlo = (double)from_key(lo2, 0.f), whi = (double)from_key(hi2, 0.f);
   int npol = 0;
   bool first = true;
   while (first || pol2) {
-    double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int e = 0; e < PEPT; ++e) {
-      if (first && fin1 && fx[e] == 0 && ka[e] > lo1) {
-        v[0] += (double)huber_d<TG>(from_key(ka[e], (TG)0), (TG)M);
-        v[1] += 1.0;
+    double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (first && fin1) {
+      const TV* av_src = mode == PM_GSTAR ? static_cast<const TV*>(a.vin) : nullptr;
+      for (int e = 0; e < PEPT; ++e) {
+        if (fx[e] != 0) continue;
+        const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+        const double aa = av_src ? fabs((double)av_src[j]) : fabs(gg[e]) / (2.0 * lam2);
+        const double hv = huber_d<double>(aa, M) - htstar;
+        if (hv > 0.0) v[0] += hv;
       }
-      if (pol2 && (double)bm[e] > wcur) {
-        v[2] += 1.0;
-        v[3] += (double)bm[e];
-        v[4] += (double)bm[e] * (double)bm[e];
+    }
+    if (pol2) {
+      for (int e = 0; e < PEPT; ++e) {
+        if ((double)bm[e] > wcur) {
+          v[2] += 1.0;
+          v[3] += (double)bm[e];
+          v[4] += (double)bm[e] * (double)bm[e];
+        }
       }
     }
     gsum(v, 5);
-    if (first && fin1) {
-      const double tstar = (double)from_key(lo1, (TG)0);
-      topsum = v[0] + ((double)kb - v[1]) * huber_d<double>(tstar, M);
-    }
+    if (first && fin1) topsum = (double)kb * htstar + v[0];
     first = false;
     if (pol2) {
       // classification at wcur: N_above, S_above, Q_above
       const double Nab = v[2], Sab = v[3], Qab = v[4];
       const double Sbel = tot[2] - Sab;
-      const double wn = Sbel / ((double)kb - Nab);
-      const bool stable = (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
-      if (stable || npol >= MAX_POLISH) {
-        gval = 0.5 * (tot[1] + Qab + wn * Sbel);
+      if ((double)kb - Nab <= 0.5) {   // budget filled by coordinates above: no water level
+        gval = 0.5 * (tot[1] + tot[3]);
         pol2 = false;
       } else {
-        nprev = Nab;
-        wcur = wn;
-        ++npol;
+        const double wn = Sbel / ((double)kb - Nab);
+        const bool stable = (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
+        if (stable || npol >= MAX_POLISH) {
+          gval = 0.5 * (tot[1] + Qab + wn * Sbel);
+          pol2 = false;
+        } else {
+          nprev = Nab;
+          wcur = wn;
+          ++npol;
+        }
       }
     }
   }
@@ -456,11 +502,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       mu = (tau - 1.0) / tn;
       tau_new = tn;
     }
-    if (isfinite(phi_best) && phi_best - psi_best <= a.tol * fmax(1.0, fabs(phi_best))) stop = true;
+    if (isfinite(phi_best) && phi_best - psi_best <= st->tol * fmax(1.0, fabs(phi_best))) stop = true;
     if (t >= a.max_iters) stop = true;
   }
 
-  // best iterates (also on the stopping iteration)
+  // best iterates (also on the stopping iteration); for the best dual value the
+  // loop's own dual point (z^t) is kept, so that the FP64 certificate
+  // evaluates Psi at exactly that point
   if (mode == PM_ITER && (imp_p || imp_d)) {
     TV* bbest = static_cast<TV*>(st->beta_best);
     TV* bdbest = static_cast<TV*>(st->beta_dbest);
@@ -471,13 +519,19 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       if (imp_p) bbest[j] = bt[e];
       if (imp_d) bdbest[j] = bt[e];
     }
+    if (imp_d) {
+      const double* zt = static_cast<const double*>(st->z_cur);
+      double* zb = static_cast<double*>(st->z_dbest);
+      for (int64_t i = gt; i < a.n; i += nthr) zb[i] = zt[i];
+    }
   }
 
   // ---------------------------------------------------------------- P1
   const bool do_prox = (mode == PM_PROX) || (mode == PM_ITER && !stop);
   TV vv[PEPT];
   TV mm[PEPT];      // |v| on Jf
-  TV ti[PEPT];      // T^{-1}(|v|): where coordinate j reaches z_j = 1
+  float mmf[PEPT];  // |v| rounded to FP32 (rounds)
+  float ti[PEPT];   // T^{-1}(|v|) in FP32: where coordinate j reaches z_j = 1
   double nzv = 0.0;
   if (do_prox) {
     const TV* vin = static_cast<const TV*>(a.vin);
@@ -486,15 +540,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
 #pragma unroll
     for (int e = 0; e < PEPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
-      vv[e] = (TV)0; mm[e] = (TV)0; ti[e] = (TV)0;
+      vv[e] = (TV)0; mm[e] = (TV)0; mmf[e] = 0.f; ti[e] = 0.f;
       if (j >= p) continue;
       TV v;
       if (mode == PM_ITER) {
         const TV b = bt[e];
         const TV bp = bprev[j];
         const TV y = b + muv * (b - bp);
-        TG gyv;
-        if (a.loss == 0) gyv = ((TG)1 + (TG)mu) * gg[e] - (TG)mu * Gprev[j];
+        double gyv;
+        if (a.loss == 0) gyv = (1.0 + mu) * gg[e] - mu * Gprev[j];
         else gyv = (mu == 0.0) ? gg[e] : gy[e];
         v = y - sv * (TV)gyv;
       } else {
@@ -504,8 +558,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       if (fx[e] == 0) {
         const TV m = v < (TV)0 ? -v : v;
         mm[e] = m;
+        mmf[e] = (float)m;
         const double md = (double)m;
-        ti[e] = (TV)((md <= M * (1.0 + rho)) ? md * (rho / (1.0 + rho)) : md - M);
+        ti[e] = (float)((md <= M * (1.0 + rho)) ? md * (rho / (1.0 + rho)) : md - M);
         if (m > (TV)0) nzv += 1.0;
       }
     }
@@ -517,7 +572,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   if (do_prox) {
     gsum(&nzv, 1);
     bool s3 = false;
-    KV lo3 = 0, hi3 = (KV)KeyOf<TV>::kInf;
+    KV lo3 = 0, hi3 = (KV)KeyOf<float>::kInf;
     double cmlo = nzv, cmhi = 0.0, ctlo = nzv, cthi = 0.0;   // #{m > lo}, #{m > hi}, same for T^-1
     if (kb <= 0) c = INFINITY;
     else if (nzv <= (double)kb) c = 0.0;
@@ -526,18 +581,18 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     while (s3) {
       unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
       const KV x3 = cand<KV>(lo3, hi3, lane);
-      const TV cq = from_key(x3, (TV)0);
+      const float cq = from_key(x3, 0.f);
       const double cqd = (double)cq;
       const double wq = fmin(cqd / rho, M);
-      const TV invw = (TV)(1.0 / wq);
+      const float invw = (float)(1.0 / wq);
       for (int src = 0; src < 32; ++src) {
 #pragma unroll
         for (int e = 0; e < PEPT; ++e) {
-          const TV m = __shfl_sync(0xffffffffu, mm[e], src);
-          const TV tv = __shfl_sync(0xffffffffu, ti[e], src);
+          const float m = __shfl_sync(0xffffffffu, mmf[e], src);
+          const float tv = __shfl_sync(0xffffffffu, ti[e], src);
           if (m > cq) {
-            const TV z = (m - cq) * invw;
-            fld[F_S3Z] += fixp(z < (TV)1 ? z : (TV)1);
+            const float z = (m - cq) * invw;
+            fld[F_S3Z] += fixp(z < 1.f ? z : 1.f);
             fld[F_S3CM] += 1ull;
           }
           fld[F_S3CT] += (tv > cq) ? 1ull : 0ull;
@@ -555,18 +610,18 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
         else if (xq < nhi) { nhi = xq; nmhi = cm; nthi = ct; }
       }
       lo3 = nlo; hi3 = nhi; cmlo = nmlo; cmhi = nmhi; ctlo = ntlo; cthi = nthi;
-      const double clo = (double)from_key(lo3, (TV)0), chi = (double)from_key(hi3, (TV)0);
+      const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
       const bool regime_inside = (rhoM > clo && rhoM <= chi);
       if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
     }
     if (kb > 0 && nzv > (double)kb) {
       // exact finishing on the bracket's piece, polished until stable
-      const double clo = (double)from_key(lo3, (TV)0), chi = (double)from_key(hi3, (TV)0);
+      const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
       double ccur = chi;
       double ntop_prev = -1.0, nmid_prev = -1.0;
       for (int it = 0; it <= MAX_POLISH; ++it) {
         const double Tc = (ccur <= rhoM) ? ccur * (1.0 + rho) / rho : ccur + M;
-        double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int e = 0; e < PEPT; ++e) {
           if (fx[e] != 0) continue;
           const double m = (double)mm[e];
