@@ -22,6 +22,7 @@ thread_local char g_detail[256] = "";
 
 void set_detail(const char* what, cudaError_t e, int line) {
   snprintf(g_detail, sizeof(g_detail), "%s failed: %s (api.cu:%d)", what, cudaGetErrorString(e), line);
+  (void)cudaGetLastError();   // a non-sticky error must not surface again in a later call
 }
 
 #define CU(call)                                                \
@@ -225,14 +226,13 @@ struct relax_handle {
   int xk_loop = XK_F32;
   void* y = nullptr;
   // plans
-  XBPlan pl_loop, pl_cert, pl_certz, pl_ident;
+  XSPlan pl_loop, pl_cert, pl_certz, pl_ident;
   PPlan pp_iter, pp_eval;
   // buffers
-  double* xpart = nullptr;       // [n][nchunk][NF] row-chunk partials of the pass
-  double* xr = nullptr;          // [2][n] link values
-  double* xg = nullptr;          // [2][p] X' r
+  double* xpart = nullptr;       // [Gc][n][NF] strip partials of the pass
+  double* xg = nullptr;          // [Gr][2][p] X' r per row group
   double* lterm = nullptr;       // [n][2] certification loss terms
-  unsigned* xcnt = nullptr;      // pass counters: done[nblk] | bdone[nblk] | rowcnt[n]
+  unsigned* xcnt = nullptr;      // pass block counters cnt[nblk]
   IterState* st = nullptr;
   PassState* ps_aux = nullptr;
   void* vb[13] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
@@ -258,7 +258,7 @@ void handle_free(relax_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xpart, h->xr, h->xg, h->lterm, h->xcnt, h->st,
+  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xpart, h->xg, h->lterm, h->xcnt, h->st,
                   h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (void* q : h->vb) if (q) cudaFree(q);
@@ -275,41 +275,40 @@ relax_status alloc(void** p, size_t bytes) {
   return RELAX_OK;
 }
 
-XBArgs pass_args(relax_handle* h, const XBPlan& pl, int link, PassState* ps) {
-  XBArgs a{};
+XSArgs pass_args(relax_handle* h, const XSPlan& pl, int link, PassState* ps) {
+  XSArgs a{};
   const bool lowp = (pl.xk == XK_BF16 || pl.xk == XK_FP8);
-  a.X = lowp ? h->Xq : h->X;
-  a.ldx = lowp ? h->ldq : h->ldx;
+  a.tm = pl.tm;
   a.n = h->n;
   a.p = h->p;
-  a.cw = pl.cw;
-  a.nchunk = pl.nchunk;
+  a.Gc = pl.Gc;
+  a.Gr = pl.Gr;
+  a.sw = pl.sw;
+  a.inner = pl.inner;
+  a.nbox = pl.nbox;
+  a.boxb = pl.boxb;
   a.B = pl.B;
   a.nblk = pl.nblk;
+  a.SA = pl.SA;
+  a.SB = pl.SB;
   a.lag = pl.lag;
-  a.sw = pl.sw;
-  a.beta_smem = pl.beta_smem;
   a.link = link;
   a.y = (const double*)h->y;
   a.colscale = lowp ? h->colscale : nullptr;
   a.ps = ps;
   a.part = h->xpart;
-  a.r = h->xr;
   a.g = h->xg;
   a.lterm = nullptr;
-  a.done = h->xcnt;
-  a.bdone = h->xcnt + pl.nblk;
-  a.rowcnt = h->xcnt + 2 * pl.nblk;
+  a.cnt = h->xcnt;
   a.status = h->status;
   a.limit_ns = h->limit_ns;
   return a;
 }
 
-// one fused pass (counters of this plan zeroed first, rowcnt included)
-cudaError_t run_pass(relax_handle* h, const XBPlan& pl, const XBArgs& a, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(h->xcnt + 2 * pl.nblk, 0, sizeof(unsigned) * (size_t)h->n, st);
-  if (e != cudaSuccess) return e;
-  return xblock_launch(pl, a, st);
+// one fused pass (its block counters are zeroed first)
+cudaError_t run_pass(relax_handle* h, const XSPlan& pl, const XSArgs& a, cudaStream_t st) {
+  (void)h;
+  return xstrip_launch(pl, a, st);
 }
 
 PArgs base_pargs(relax_handle* h) {
@@ -345,10 +344,10 @@ relax_status power_iteration(relax_handle* h, double* L_out) {
     ps.zout = h->vb[10];
     *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;   // staging in pinned memory
     CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-    XBArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux);
+    XSArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux);
     CU(run_pass(h, h->pl_ident, a, h->stream));
     CU(cudaMemsetAsync(h->dscr, 0, 2 * sizeof(double), h->stream));
-    reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, 1, 1, h->p, w, h->dscr);
+    reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, h->pl_ident.Gr, 1, h->p, w, h->dscr);
     sumsq_kernel<<<grid_for(h->n), 256, 0, h->stream>>>((const double*)h->vb[10], h->n, h->dscr + 1);
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -386,7 +385,7 @@ relax_status count_fixings(relax_handle* h, const int8_t* fix, int* j1, int* jf)
 // zeta = -grad F(X beta_d) when zd == NULL, else zeta = -grad F(zd) (a dual
 // point given by its z).
 relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd, const void* zd) {
-  const XBPlan& pl = zd ? h->pl_certz : h->pl_cert;
+  const XSPlan& pl = zd ? h->pl_certz : h->pl_cert;
   PassState ps{};
   ps.beta = bp;
   ps.beta2 = zd ? nullptr : bd;
@@ -395,9 +394,7 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
   CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
   const int link = zd ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
                       : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
-  XBArgs a = pass_args(h, pl, link, h->ps_aux);
-  a.X = h->X;
-  a.ldx = h->ldx;
+  XSArgs a = pass_args(h, pl, link, h->ps_aux);
   a.colscale = nullptr;
   a.lterm = h->lterm;
   CU(run_pass(h, pl, a, h->stream));
@@ -405,7 +402,7 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
   pa.mode = PM_EVAL;
   pa.fix = fix;
   pa.part = h->xg;
-  pa.ncl = 1;
+  pa.ncl = pl.Gr;
   pa.NB = 1;
   pa.st = nullptr;
   pa.vin = bp;
@@ -533,30 +530,39 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       }
     }
     const bool vd = dtype == RELAX_F64;
-    TRYC(xblock_plan(h->pl_loop, h->xk_loop, false, 1, loss == RELAX_LS ? 1 : 2, n, p));
-    TRYC(xblock_plan(h->pl_ident, h->xk_loop, false, 1, 1, n, p));
-    TRYC(xblock_plan(h->pl_cert, vd ? XK_F64 : XK_F32, true, 2, 1, n, p));
-    TRYC(xblock_plan(h->pl_certz, vd ? XK_F64 : XK_F32, true, 1, 1, n, p));
+    TRYC(xstrip_plan(h->pl_loop, h->xk_loop, false, 1, loss == RELAX_LS ? 1 : 2, n, p));
+    TRYC(xstrip_plan(h->pl_ident, h->xk_loop, false, 1, 1, n, p));
+    TRYC(xstrip_plan(h->pl_cert, vd ? XK_F64 : XK_F32, true, 2, 1, n, p));
+    TRYC(xstrip_plan(h->pl_certz, vd ? XK_F64 : XK_F32, true, 1, 1, n, p));
+    {
+      const bool lowp = h->xk_loop == XK_BF16 || h->xk_loop == XK_FP8;
+      const void* xl = lowp ? h->Xq : h->X;
+      const int64_t ldl = lowp ? h->ldq : h->ldx;
+      TRYC(xstrip_bind(h->pl_loop, xl, ldl, n, p));
+      TRYC(xstrip_bind(h->pl_ident, xl, ldl, n, p));
+      TRYC(xstrip_bind(h->pl_cert, h->X, h->ldx, n, p));
+      TRYC(xstrip_bind(h->pl_certz, h->X, h->ldx, n, p));
+    }
     if (std::getenv("RELAX_DEBUG")) {
-      const XBPlan& q = h->pl_loop;
-      std::fprintf(stderr, "[relax] loop pass: xk=%d B=%d nblk=%d lag=%d nchunk=%d cw=%lld sw=%lld grid=%d smem=%zu beta_smem=%d\n",
-                   q.xk, q.B, q.nblk, q.lag, q.nchunk, (long long)q.cw, (long long)q.sw, q.grid, q.smem, q.beta_smem);
+      const XSPlan& q = h->pl_loop;
+      std::fprintf(stderr, "[relax] loop pass: xk=%d Gc=%d Gr=%d sw=%lld (%d x %d) B=%d nblk=%d SA=%d SB=%d lag=%d threads=%d smem=%zu\n",
+                   q.xk, q.Gc, q.Gr, (long long)q.sw, q.nbox, q.inner, q.B, q.nblk, q.SA, q.SB, q.lag, q.threads, q.smem);
     }
     TRYC(pphase_plan(h->pp_iter, true, p));
     TRYC(pphase_plan(h->pp_eval, true, p));
     {
-      const XBPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
+      const XSPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
       size_t part_n = 0;
-      int nblk_max = 0;
-      for (const XBPlan* q : pls) {
-        part_n = std::max(part_n, (size_t)n * q->nchunk * q->NF);
+      int nblk_max = 0, gr_max = 1;
+      for (const XSPlan* q : pls) {
+        part_n = std::max(part_n, (size_t)n * q->Gc * q->NF);
+        gr_max = std::max(gr_max, q->Gr);
         nblk_max = std::max(nblk_max, q->nblk);
       }
       TRY(alloc((void**)&h->xpart, part_n * sizeof(double)));
-      TRY(alloc((void**)&h->xr, (size_t)2 * n * sizeof(double)));
-      TRY(alloc((void**)&h->xg, (size_t)2 * p * sizeof(double)));
+      TRY(alloc((void**)&h->xg, (size_t)gr_max * 2 * p * sizeof(double)));
       TRY(alloc((void**)&h->lterm, (size_t)2 * n * sizeof(double)));
-      TRY(alloc((void**)&h->xcnt, ((size_t)2 * nblk_max + n) * sizeof(unsigned)));
+      TRY(alloc((void**)&h->xcnt, (size_t)nblk_max * sizeof(unsigned)));
     }
     TRY(alloc((void**)&h->st, sizeof(IterState)));
     TRY(alloc((void**)&h->ps_aux, sizeof(PassState)));
@@ -639,12 +645,12 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
   // ---- one iteration = fused X-pass + p-phase; enqueue `chunk` per host poll
-  XBArgs xa = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps);
+  XSArgs xa = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps);
   PArgs pa = base_pargs(h);
   pa.mode = PM_ITER;
   pa.fix = fixings;
   pa.part = h->xg;
-  pa.ncl = 1;
+  pa.ncl = h->pl_loop.Gr;
   pa.NB = h->pl_loop.NB;
   pa.st = h->st;
   pa.bar = h->bar;
@@ -834,10 +840,10 @@ relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g
   CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
   CU(cudaMemsetAsync(zp64, 0, (size_t)h->n * sizeof(double), h->stream));
-  XBArgs a = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, h->ps_aux);
+  XSArgs a = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, h->ps_aux);
   CU(run_pass(h, h->pl_loop, a, h->stream));
   const unsigned g = grid_for(h->p);
-  reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, 1, h->pl_loop.NB, h->p, g64, nullptr);
+  reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, h->pl_loop.Gr, h->pl_loop.NB, h->p, g64, nullptr);
   from_f64_kernel<<<g, 256, 0, h->stream>>>(g64, g_out, h->f64(), h->p);
   if (z_out) from_f64_kernel<<<grid_for(h->n), 256, 0, h->stream>>>(z64, z_out, h->f64(), h->n);
   CU(cudaMemsetAsync(h->dscr, 0, 2 * sizeof(double), h->stream));

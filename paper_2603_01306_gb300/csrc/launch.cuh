@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "pphase.cuh"
-#include "xblock.cuh"
+#include "xstrip.cuh"
 #include "xpass.cuh"
 
 namespace relax {
@@ -14,23 +14,26 @@ enum XKind : int { XK_F64 = 0, XK_F32 = 1, XK_BF16 = 2, XK_FP8 = 3 };
 inline int xkind_esize(int xk) { return xk == XK_F64 ? 8 : xk == XK_F32 ? 4 : xk == XK_BF16 ? 2 : 1; }
 inline int xkind_vec(int xk) { return 16 / xkind_esize(xk); }
 
-// Fused pass by L2 row blocking (xblock.cuh)
-struct XBPlan {
+// Strip-stationary fused pass (xstrip.cuh)
+struct XSPlan {
+  CUtensorMap tm{};        // the plan's X as a tensor (set by xstrip_bind)
   int xk = 0;
-  bool cert = false;       // FP64 accumulation (certification / power iteration of FP64 data)
+  bool cert = false;       // FP64 accumulation (certification / power iteration of FP32 data)
   int NF = 1, NB = 1;
-  int64_t cw = 0;          // chunk columns
-  int nchunk = 1;
-  int B = 1, nblk = 1, lag = 2;
-  int64_t sw = 0;          // strip columns per CTA
-  int beta_smem = 0;
-  int grid = 1;
+  int Gc = 1, Gr = 1;      // column strips x row groups
+  int64_t sw = 0;          // strip columns = nbox * inner
+  int inner = 1, nbox = 1, boxb = 128;
+  int B = 1, nblk = 1;     // rows per block, blocks
+  int SA = 3, SB = 3, lag = 4;
+  int grid = 1, threads = 32;
   size_t smem = 0;
   const void* kernel = nullptr;
 };
-cudaError_t xblock_plan(XBPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p);
-// counters (2 * nblk unsigned) are zeroed on the stream before the launch
-cudaError_t xblock_launch(const XBPlan& pl, const XBArgs& a, cudaStream_t st);
+cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p);
+// encode the plan's tensor map of X (16-byte aligned, ldx * size a multiple of 16)
+cudaError_t xstrip_bind(XSPlan& pl, const void* X, int64_t ldx, int64_t n, int64_t p);
+// the block counters (nblk unsigned at a.cnt) are zeroed on the stream before the launch
+cudaError_t xstrip_launch(const XSPlan& pl, const XSArgs& a, cudaStream_t st);
 
 struct PPlan {
   const void* kernel = nullptr;

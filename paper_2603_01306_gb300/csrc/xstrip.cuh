@@ -1,0 +1,536 @@
+// Fused pass over X, strip-stationary: z = X beta, r = link(z), g = X' r, with
+// X read from HBM once per pass.
+//
+// This is the matrix-vector work that dominates the method (Sec. 5.2.3); the
+// induced dual point zeta = -grad F(X beta) (Sec. 3.3) comes out of it as -r.
+//
+// Decomposition.  The grid is Gc x Gr CTAs, one per SM, co-resident.  CTA
+// (cc, cr) owns the column strip cc (a few KB of every row) and the row blocks
+// b = cr, cr + Gr, ... (B rows each).  Its strip of beta lives in registers and
+// its strip of X' r is accumulated in registers, so no CTA ever needs the whole
+// of beta or of g.
+//
+// Per CTA, warp-specialized:
+//  * lane 0 of warp 0 streams the CTA's strip tiles of its blocks from HBM into
+//    ring A (SA stages; a tile is nbox 2-D tensor boxes of B rows x `inner`
+//    columns, loaded by TMA, which zero-fills columns >= p and rows >= n);
+//    lane 16 of warp 0 loads the same tiles again, from L2, into ring B (SB
+//    stages);
+//  * SA "dot" warps (warp a owns stage a of ring A): per row the strip's partial
+//    dot product with beta, stored to part[cc][row], then counted in cnt[b];
+//  * SB "axpy" warps (warp e owns stage e of ring B): once cnt[b] = Gc each
+//    sums the Gc partials of every row of the block in a fixed order (so every
+//    CTA gets the same z, whatever the arrival order), applies the link and
+//    accumulates X' r over its strip; CTA (k mod Gc) of the row group records
+//    z and the loss terms of the group's k-th block; at the end the axpy warps'
+//    strip sums are combined in a fixed order into g[cr][q][strip].
+// Each stage has exactly one consumer warp, which therefore never waits on a
+// barrier phase more than one ahead of the last one it saw.  Phase A may lead
+// phase B by at most `lag` blocks of the CTA (L2 footprint).  Every wait is
+// bounded: on expiry the kernel records ST_TIMEOUT, stops issuing and waiting,
+// lets the copies in flight land and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "xpass.cuh"
+
+namespace relax {
+
+constexpr int XS_MAXS = 4;        // stages per ring at most (= warps per phase)
+constexpr int XS_MAXB = 16;       // rows per block at most (one butterfly group)
+constexpr int XS_MAXT = 256;      // 1 + SA + SB warps: at most two per scheduler
+// 16-byte vectors of the strip per lane: a lane holds the same number of
+// accumulators (24 FP32 or 12 FP64 columns, 24/32 for 16/8-bit X) for every type
+template <int VEC> struct XSShape {
+  static constexpr int TV = VEC == 2 ? 6 : VEC == 4 ? 6 : VEC == 8 ? 3 : 2;
+};
+
+struct XSArgs {
+  CUtensorMap tm;        // X as a 2-D tensor (p columns x n rows), box `inner` x B
+  int64_t n, p;
+  int Gc, Gr;            // column strips x row groups; grid = Gc * Gr
+  int64_t sw;            // strip columns = nbox * inner
+  int inner, nbox;       // box columns (multiple of the vector width, <= 256); boxes per strip
+  int boxb;              // bytes per box in shared memory (B * inner * size, padded to 128)
+  int B, nblk;           // rows per block, blocks
+  int SA, SB, lag;       // ring stages; lead of phase A over phase B (blocks)
+  int link;
+  const double* y;
+  const float* colscale;
+  PassState* ps;
+  double* part;          // [Gc][n][NF] strip partials (FP32 pair bits or FP64)
+  double* g;             // [Gr][NB][p] X' r per row group
+  double* lterm;         // [n][2] per-row {F, -F*(-zeta)} (certification links) or NULL
+  unsigned* cnt;         // [nblk] CTAs done with the block's dots (zeroed before the launch)
+  int* status;
+  uint64_t limit_ns;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// bounded wait until *ctr >= target; false (and ST_TIMEOUT) after limit_ns
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, uint64_t limit_ns, int* status) {
+  if (ld_acquire_u32(ctr) >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (ld_acquire_u32(ctr) >= target) return true;
+    if ((it & 15u) == 0u) {
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicCAS(status, ST_OK, ST_TIMEOUT);
+        return false;
+      }
+      __nanosleep(20);
+    }
+  }
+}
+
+// bounded wait until a shared-memory counter reaches target
+__device__ __forceinline__ bool wait_smem(const volatile unsigned* ctr, unsigned target, uint64_t limit_ns,
+                                          int* status) {
+  if (*ctr >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (*ctr >= target) return true;
+    if ((it & 15u) == 0u && globaltimer_ns() - t0 > limit_ns) {
+      atomicCAS(status, ST_OK, ST_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// 2-D tensor box (x = column, y = row) -> shared memory, completion on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// (h, l) += (rh, rl) for compensated FP32 pairs
+__device__ __forceinline__ void pair_add(float& h, float& l, float rh, float rl) {
+  float e = 0.f;
+  float s = h;
+  two_sum_acc(s, e, rh);
+  h = s;
+  l = l + rl + e;
+}
+
+// Transposed butterfly over 16 rows: on entry lane L holds its partial of
+// every row in h[0..15] (l = low parts); on exit h[0], l[0] of lane L hold the
+// warp total of row (L >> 1) & 15.  Each step sends half of the remaining rows
+// to the partner lane and keeps the other half: 8+4+2+1+1 shuffles of pairs
+// instead of 16 x 5.
+__device__ __forceinline__ void butterfly16(float (&h)[16], float (&l)[16], int lane) {
+#pragma unroll
+  for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float sh = up ? h[i] : h[i + half], sl = up ? l[i] : l[i + half];
+      const float kh = up ? h[i + half] : h[i], kl = up ? l[i + half] : l[i];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      h[i] = kh;
+      l[i] = kl;
+      pair_add(h[i], l[i], rh, rl);
+    }
+  }
+  const float rh = __shfl_xor_sync(0xffffffffu, h[0], 1), rl = __shfl_xor_sync(0xffffffffu, l[0], 1);
+  pair_add(h[0], l[0], rh, rl);
+}
+__device__ __forceinline__ void butterfly16(double (&h)[16], int lane) {
+#pragma unroll
+  for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double sh = up ? h[i] : h[i + half];
+      const double kh = up ? h[i + half] : h[i];
+      h[i] = kh + __shfl_xor_sync(0xffffffffu, sh, o);
+    }
+  }
+  h[0] += __shfl_xor_sync(0xffffffffu, h[0], 1);
+}
+
+// Link of one row: w[q] = the gradient weights of the row (r = grad F at z, and
+// at the momentum point for the logistic loop), lf = F term at z[0],
+// ld = -F*(-zeta) term of the dual point (certification links).  zp is the
+// row's entry of ps.zprev (z of the previous iterate, or the given dual point).
+template <int NF, int NB>
+__device__ __forceinline__ void link_of(int link, const double* z, double yd, double zp, double mom, double* w,
+                                        double& lf, double& ld) {
+#pragma unroll
+  for (int q = 0; q < NB; ++q) w[q] = 0.0;
+  lf = 0.0;
+  ld = 0.0;
+  switch (link) {
+    case LINK_LS:
+      w[0] = 2.0 * (z[0] - yd);
+      break;
+    case LINK_LOGISTIC:
+      w[0] = -yd / (1.0 + exp(yd * z[0]));
+      if (NB > 1) {
+        const double zy = (1.0 + mom) * z[0] - mom * zp;
+        w[NB - 1] = -yd / (1.0 + exp(yd * zy));
+      }
+      break;
+    case LINK_IDENT:
+      w[0] = z[0];
+      break;
+    case LINK_CERT_LS:
+    case LINK_CERTZ_LS: {
+      const double zd = link == LINK_CERT_LS ? z[NF - 1] : zp;
+      const double d0 = z[0] - yd, d1 = zd - yd, zeta = -2.0 * d1;
+      w[0] = 2.0 * d1;
+      lf = d0 * d0;
+      ld = zeta * yd - 0.25 * zeta * zeta;
+      break;
+    }
+    case LINK_CERT_LOGI:
+    case LINK_CERTZ_LOGI: {
+      const double zd = link == LINK_CERT_LOGI ? z[NF - 1] : zp;
+      w[0] = -yd / (1.0 + exp(yd * zd));
+      lf = softplus_neg(yd * z[0]);
+      ld = entropy_of(yd * zd);
+      break;
+    }
+    default: break;
+  }
+}
+
+template <typename TX, typename TA, int NF, int NB>
+__global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constant__ XSArgs a) {
+  constexpr int VEC = XTraits<TX>::VEC;
+  constexpr int TV = XSShape<VEC>::TV;
+  constexpr bool kF32 = sizeof(TA) == 4;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t fullA[XS_MAXS], emptyA[XS_MAXS], fullB[XS_MAXS], emptyB[XS_MAXS];
+  __shared__ volatile int tmo;        // a bounded wait expired: stop issuing and waiting
+  __shared__ volatile unsigned bcnt;  // blocks finished by phase B in this CTA
+  __shared__ int skip;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tmo = 0;
+    bcnt = 0;
+    skip = a.ps->done;
+    for (int s = 0; s < a.SA; ++s) { mbar_init(&fullA[s], 1); mbar_init(&emptyA[s], 1); }
+    for (int s = 0; s < a.SB; ++s) { mbar_init(&fullB[s], 1); mbar_init(&emptyB[s], 1); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (skip) return;   // uniform (same flag everywhere)
+
+  // tensor boxes land on 128-byte aligned addresses (128 bytes of slack are allocated)
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int cc = blockIdx.x % a.Gc, cr = blockIdx.x / a.Gc;
+  const int64_t n = a.n, p = a.p;
+  const int64_t s0 = (int64_t)cc * a.sw;
+  const int64_t s1 = (s0 + a.sw < p) ? s0 + a.sw : p;
+  const int nvs = (int)((s1 - s0 + VEC - 1) / VEC);          // vectors of the strip
+  const uint32_t tilebytes = (uint32_t)a.nbox * a.B * a.inner * (uint32_t)sizeof(TX);   // tx bytes per tile
+  const int rowpitch = a.inner * (int)sizeof(TX);   // bytes per row inside a box
+  // byte offsets of this lane's vectors in row 0 of a tile (box, then vector in
+  // the box row); lanes past the strip read its last vector (their beta is zero
+  // and their sums are never written)
+  uint32_t voff[TV];
+  {
+    const int vpb = a.inner / VEC;
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+      const int v = min(lane + 32 * t, max(nvs - 1, 0));
+      voff[t] = (uint32_t)((v / vpb) * a.boxb + (v % vpb) * 16);
+    }
+  }
+  const int kloc = (cr < a.nblk) ? (a.nblk - cr + a.Gr - 1) / a.Gr : 0;   // blocks of this CTA
+  const size_t stage = (size_t)a.nbox * a.boxb;
+  unsigned char* ringA = smem;
+  unsigned char* ringB = smem + (size_t)a.SA * stage;
+  {
+    // the fixed-shape row loops read every row of a tile; keep never-loaded
+    // stage memory finite
+    float4* z4 = reinterpret_cast<float4*>(smem);
+    const size_t nz = (size_t)(a.SA + a.SB) * stage / 16;
+    for (size_t i = tid; i < nz; i += blockDim.x) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+  }
+  // phase-B accumulators (used by the axpy warps only)
+  TA acc[NB][TV][VEC];
+  float ahi[kF32 ? NB : 1][TV][VEC], alo[kF32 ? NB : 1][TV][VEC];
+  const bool axpy = warp >= 1 + a.SA && warp < 1 + a.SA + a.SB;
+
+  if (warp == 0) {
+    // ------------------------------------------------ producer A: HBM -> ring A
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_normal();
+      int issued = 0;
+      for (int k = 0; k < kloc; ++k) {
+        const int s = k % a.SA;
+        if (tmo) break;
+        if (k >= a.SA && !mbar_wait<false>(&emptyA[s], ((k / a.SA) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
+        if (k > a.lag && !wait_smem(&bcnt, (unsigned)(k - a.lag), a.limit_ns, a.status)) { tmo = 1; break; }
+        const int y0 = (cr + k * a.Gr) * a.B;
+        mbar_arrive_expect_tx(&fullA[s], tilebytes);
+        for (int i = 0; i < a.nbox; ++i)
+          tma_load_2d(ringA + s * stage + (size_t)i * a.boxb, &a.tm, (int)s0 + i * a.inner, y0, &fullA[s], pol);
+        issued = k + 1;
+      }
+      // let every copy in flight land before the CTA may exit
+      for (int k = (issued > a.SA ? issued - a.SA : 0); k < issued; ++k)
+        mbar_wait<false>(&fullA[k % a.SA], (k / a.SA) & 1, a.limit_ns, a.status);
+    }
+    // ------------------------------------------------- producer B: L2 -> ring B
+    if (lane == 16) {
+      const uint64_t pol = policy_evict_first();
+      int issued = 0;
+      for (int k = 0; k < kloc; ++k) {
+        const int s = k % a.SB;
+        if (tmo) break;
+        if (k >= a.SB && !mbar_wait<false>(&emptyB[s], ((k / a.SB) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
+        const int y0 = (cr + k * a.Gr) * a.B;
+        mbar_arrive_expect_tx(&fullB[s], tilebytes);
+        for (int i = 0; i < a.nbox; ++i)
+          tma_load_2d(ringB + s * stage + (size_t)i * a.boxb, &a.tm, (int)s0 + i * a.inner, y0, &fullB[s], pol);
+        issued = k + 1;
+      }
+      for (int k = (issued > a.SB ? issued - a.SB : 0); k < issued; ++k)
+        mbar_wait<false>(&fullB[k % a.SB], (k / a.SB) & 1, a.limit_ns, a.status);
+    }
+  } else if (warp < 1 + a.SA) {
+    // ------------------------------------------------ phase A: strip dot products
+    const int st = warp - 1;
+    TA bv[NF][TV][VEC];
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+      const int v = lane + 32 * t;
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int64_t col = s0 + (int64_t)v * VEC + l;
+        const bool in = v < nvs && col < p;
+        const double sc = (in && a.colscale) ? (double)a.colscale[col] : 1.0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          bv[f][t][l] = in ? (TA)(static_cast<const double*>(f == 0 ? a.ps->beta : a.ps->beta2)[col] * sc) : (TA)0;
+      }
+    }
+    for (int k = st; k < kloc; k += a.SA) {
+      if (tmo) break;
+      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullA[st], (k / a.SA) & 1, a.limit_ns, a.status))) {
+        tmo = 1;
+        break;
+      }
+      const int b = cr + k * a.Gr;
+      const int64_t r0 = (int64_t)b * a.B;
+      const int rows = (int)((n - r0) < a.B ? (n - r0) : a.B);
+      const unsigned char* tile = ringA + st * stage;
+      // per-lane partials of the block's rows (plain FP32 over the lane's
+      // columns), then one transposed butterfly per forward vector
+      TA ph[NF][XS_MAXB];
+#pragma unroll
+      for (int jj = 0; jj < XS_MAXB; ++jj) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) ph[f][jj] = (TA)0;
+        const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
+        const unsigned char* rowp = tile + (size_t)jr * rowpitch;
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+          TA x[VEC];
+          XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
+        }
+      }
+      double mine[NF];   // lane 2j: the strip partial of row j
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if constexpr (kF32) {
+          float pl[XS_MAXB];
+#pragma unroll
+          for (int jj = 0; jj < XS_MAXB; ++jj) pl[jj] = 0.f;
+          butterfly16(ph[f], pl, lane);
+          mine[f] = pack_pair(ph[f][0], pl[0]);
+        } else {
+          butterfly16(ph[f], lane);
+          mine[f] = ph[f][0];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyA[st]);   // stage free: the rest works on registers
+      if ((lane & 1) == 0 && (lane >> 1) < rows) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a.part[((size_t)cc * n + r0 + (lane >> 1)) * NF + f] = mine[f];
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(&a.cnt[b], 1u);
+    }
+  } else if (axpy) {
+    // ------------------------------------------------ phase B: X' r over the strip
+    const int st = warp - 1 - a.SA;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int t = 0; t < TV; ++t)
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+          acc[q][t][l] = (TA)0;
+          if constexpr (kF32) { ahi[q][t][l] = 0.f; alo[q][t][l] = 0.f; }
+        }
+    const bool need_zp = a.link == LINK_CERTZ_LS || a.link == LINK_CERTZ_LOGI || (a.link == LINK_LOGISTIC && NB > 1);
+    const double* zprev = static_cast<const double*>(a.ps->zprev);
+    double* zout = static_cast<double*>(a.ps->zout);
+    const double mom = a.ps->mom;
+    // lane = 16 hb + j: row j of the block, strips cc = 2i + hb
+    const int jl = lane & 15, hb = lane >> 4;
+    const int npl = (a.Gc - hb + 1) / 2;   // strips this lane sums
+    for (int k = st; k < kloc; k += a.SB) {
+      if (tmo) break;
+      const int b = cr + k * a.Gr;
+      const int64_t r0 = (int64_t)b * a.B;
+      const int rows = (int)((n - r0) < a.B ? (n - r0) : a.B);
+      const int64_t rowj = r0 + (jl < rows ? jl : rows - 1);
+      const double yd = a.y[rowj];
+      const double zp = need_zp ? zprev[rowj] : 0.0;
+      if (!__all_sync(0xffffffffu, wait_count(&a.cnt[b], (unsigned)a.Gc, a.limit_ns, a.status))) {
+        tmo = 1;
+        break;
+      }
+      // z of row j: the Gc strip partials in a fixed order (even strips, odd
+      // strips, then even + odd), identical in every CTA
+      double z[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const double* pr = a.part + ((size_t)hb * n + rowj) * NF + f;
+        const size_t step = (size_t)2 * n * NF;
+        constexpr int U = 20;
+        if constexpr (kF32) {
+          float h = 0.f, l = 0.f;
+          for (int i0 = 0; i0 < npl; i0 += U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = (i0 + u < npl) ? __ldcg(pr + (size_t)(i0 + u) * step) : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) add_pair(h, l, v[u]);
+          }
+          const float oh = __shfl_xor_sync(0xffffffffu, h, 16), ol = __shfl_xor_sync(0xffffffffu, l, 16);
+          float eh = hb ? oh : h, el = hb ? ol : l;   // even strips' sum first
+          pair_add(eh, el, hb ? h : oh, hb ? l : ol);
+          z[f] = (double)eh + (double)el;
+        } else {
+          double sum = 0.0;
+          for (int i0 = 0; i0 < npl; i0 += U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = (i0 + u < npl) ? __ldcg(pr + (size_t)(i0 + u) * step) : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) sum += v[u];
+          }
+          const double other = __shfl_xor_sync(0xffffffffu, sum, 16);
+          z[f] = hb ? other + sum : sum + other;
+        }
+      }
+      double rv[NB], lf, ld;
+      link_of<NF, NB>(a.link, z, yd, zp, mom, rv, lf, ld);
+      if (jl >= rows) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) rv[q] = 0.0;   // rows past the end carry weight 0
+      }
+      if (cc == k % a.Gc && hb == 0 && jl < rows) {   // this CTA records the block
+        if (zout) zout[r0 + jl] = z[0];
+        if (a.lterm) { a.lterm[2 * (r0 + jl)] = lf; a.lterm[2 * (r0 + jl) + 1] = ld; }
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullB[st], (k / a.SB) & 1, a.limit_ns, a.status))) {
+        tmo = 1;
+        break;
+      }
+      const unsigned char* tile = ringB + st * stage;
+#pragma unroll
+      for (int j = 0; j < XS_MAXB; ++j) {
+        const int jr = j < a.B ? j : a.B - 1;   // rows >= rows carry weight 0
+        TA w[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) w[q] = (TA)__shfl_sync(0xffffffffu, rv[q], j);
+        const unsigned char* rowp = tile + (size_t)jr * rowpitch;
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+          TA x[VEC];
+          XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+          for (int l = 0; l < VEC; ++l)
+#pragma unroll
+            for (int q = 0; q < NB; ++q) acc[q][t][l] += w[q] * x[l];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&emptyB[st]);
+        atomicAdd((unsigned*)&bcnt, 1u);
+      }
+      if constexpr (kF32) {   // fold the block's FP32 sums into the compensated pair
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+#pragma unroll
+          for (int t = 0; t < TV; ++t)
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+              two_sum_acc(ahi[q][t][l], alo[q][t][l], (float)acc[q][t][l]);
+              acc[q][t][l] = (TA)0;
+            }
+      }
+    }
+  }
+  __syncthreads();   // every copy has landed: the rings are free
+  const int wcols = nvs * VEC;
+  double* comb = reinterpret_cast<double*>(smem);   // [SB][NB][wcols] strip sums of the axpy warps
+  if (axpy) {
+    const int st = warp - 1 - a.SA;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int t = 0; t < TV; ++t)
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+          const int e = (lane + 32 * t) * VEC + l;
+          if (e < wcols) {
+            const double v = kF32 ? (double)ahi[q][t][l] + (double)alo[q][t][l] : (double)acc[q][t][l];
+            comb[((size_t)st * NB + q) * wcols + e] = v;
+          }
+        }
+  }
+  __syncthreads();
+  // fixed-order sum of the SB warps' strip sums -> g[cr][q][s0 + e]
+  const int64_t ncol = s1 - s0;
+  for (int64_t e = tid; e < ncol; e += blockDim.x) {
+    const double sc = a.colscale ? (double)a.colscale[s0 + e] : 1.0;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      double sum = 0.0;
+      for (int w = 0; w < a.SB; ++w) sum += comb[((size_t)w * NB + q) * wcols + e];
+      a.g[((size_t)cr * NB + q) * p + s0 + e] = sum * sc;
+    }
+  }
+}
+
+}  // namespace relax
