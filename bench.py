@@ -6,6 +6,10 @@ M = 2) solved to relative gap 1e-6 through the C ABI (fused X-pass + p-phase per
 FISTA iteration, gap restarts, FP64 certification at the end), inputs resident
 in HBM.  X (4 GB) is larger than L2, so no flush is needed between steps.
 
+e2e: the same relaxation end to end through the public API from pinned host
+buffers: X and y copied to the device, handle created (Lipschitz constant by
+power iteration), solved, beta copied back, handle destroyed.
+
 Multi-GPU: one process per GPU (torchrun), each rank solves its own replica of
 the workload; no data-path collective (the path shards by independent node
 problems).  value = relaxations of all ranks / max over ranks of the timed span.
@@ -35,9 +39,9 @@ WORKLOAD = "ls_20000x50000_f32"
 GAP_TOL = 1e-6
 # FISTA iterations the GPU solve of WORKLOAD needs to reach GAP_TOL (measured on
 # GB300 by this script's own arm; used by --impl reference to extrapolate).
-GPU_ITERS_TO_GAP = {"ls_20000x50000_f32": None}
+GPU_ITERS_TO_GAP = {"ls_20000x50000_f32": 929}
 METRIC = "node relaxations/s to rel. gap 1e-6 on 1 GB300; fused X-pass HBM GB/s vs peak"
-PROFILE = os.path.join(ROOT, "profiles", "xpass_ls_20000x50000_f32.json")
+PROFILE = os.path.join(ROOT, "profiles", "xstrip_ls_20000x50000_f32.md")
 
 
 def env_rank():
@@ -54,21 +58,29 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("xpass.cuh", "common.cuh"):
+    for f in ("xstrip.cuh", "xpass.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2603_01306_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profile_traffic():
-    """DRAM bytes per X-pass launch from the committed ncu summary, or None when
-    the kernel source changed since the counters were taken."""
+    """DRAM bytes per X-pass launch from the committed ncu summary (its
+    "key: value" lines), or None when the kernel source changed since the
+    counters were taken."""
     try:
-        prof = json.load(open(PROFILE))
+        kv = {}
+        for line in open(PROFILE):
+            if ":" in line and not line.startswith(("#", " ", "|")):
+                k, v = line.split(":", 1)
+                kv[k.strip("- *`").strip()] = v.strip(" `\n")
     except Exception:
         return None
-    if prof.get("kernel_source_hash") != kernel_source_hash():
+    if kv.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return prof.get("dram_bytes_per_launch")
+    try:
+        return float(kv["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -127,9 +139,9 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def make_inputs(device):
+def make_inputs(device, workload=WORKLOAD):
     import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[workload]
     X, y = synth.make_problem_gpu(w, device=device)
     return w, X, y
 
@@ -145,7 +157,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(device))
     relax.load()
-    w, X, y = make_inputs(device)
+    w, X, y = make_inputs(device, args.workload)
     h = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M, timing=True)
     stream = torch.cuda.current_stream()
     beta = torch.empty(w.p, dtype=torch.float32, device=device)
@@ -177,26 +189,31 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
-    # ---- end to end through the public API: per-step node inputs from pinned host memory
-    fix_h = torch.zeros(w.p, dtype=torch.int8).pin_memory()
-    warm_h = torch.zeros(w.p, dtype=torch.float32).pin_memory()
+    clocks = clk.summary()
+    # ---- end to end through the public API, from pinned host buffers
+    X_h = torch.empty(tuple(X.shape), dtype=torch.float32).pin_memory()
+    y_h = torch.empty(tuple(y.shape), dtype=torch.float32).pin_memory()
+    X_h.copy_(X)
+    y_h.copy_(y)
     beta_h = torch.empty(w.p, dtype=torch.float32).pin_memory()
-    fix_d = torch.empty(w.p, dtype=torch.int8, device=device)
-    warm_d = torch.empty(w.p, dtype=torch.float32, device=device)
+    h.close()
+    del X, y
+    torch.cuda.empty_cache()
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, args.e2e_steps)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fix_d.copy_(fix_h, non_blocking=True)
-        warm_d.copy_(warm_h, non_blocking=True)
-        _, res, code = h.solve(fixings=fix_d, warm_start=warm_d, gap_tol=GAP_TOL, beta_out=beta)
+        Xd = X_h.to(device, non_blocking=True)
+        yd = y_h.to(device, non_blocking=True)
+        he = relax.Handle(Xd, yd, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M)
+        _, res_e, code = he.solve(gap_tol=GAP_TOL, beta_out=beta)
         beta_h.copy_(beta, non_blocking=True)
         torch.cuda.synchronize()
+        he.close()
+        del Xd, yd
         if code != 0:
             raise RuntimeError(f"solve status {relax.STATUS[code]}")
     e2e_s = time.perf_counter() - t0
-    clocks = clk.summary()
-    h.close()
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -225,7 +242,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded AR(1) Gaussian design, generated on the device)",
-        "config": {"workload": WORKLOAD, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2,
+        "config": {"workload": args.workload, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2,
                    "rho": w.rho, "loss": w.loss, "M": w.M, "gap_tol": GAP_TOL, "snr": w.snr,
                    "l2": "inputs larger than L2 (X is 4 GB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -235,21 +252,21 @@ def run_ours(args):
         "lipschitz": results[-1].lipschitz,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "xpass_kernel (fused X beta / link / X' r)",
+                     "kernel": "xstrip_kernel (fused X beta / link / X' r)",
                      "avg_launch_ms": avg_ms, "launches_timed": xp_n,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
                      else "fallback 6800 GB/s (of fallback)"},
         "pphase_ms_per_iter": pp_ms / max(1, xp_n),
-        "e2e": {"value": e2e_steps / e2e_s, "unit": "relaxations/s",
-                "h2d_bytes_per_step": w.p * 1 + w.p * 4, "d2h_bytes_per_step": w.p * 4,
-                "note": "per-node inputs (fixings, warm start) copied from pinned host each step; "
-                        "X resident across node solves as in branch and bound"},
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "relaxations/s",
+                "h2d_bytes_per_step": w.n * w.p * 4 + w.n * 4, "d2h_bytes_per_step": w.p * 4,
+                "steps": e2e_steps,
+                "note": "X, y from pinned host; handle create (power iteration), solve, beta to host, destroy"},
         "clocks": clocks,
         "gpu_launches": sum(r.launches for r in results),
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(X, y, w, results[-1].lipschitz, statistics.median(iters),
+        line["cpu_baseline"] = cpu_baseline(X_h, y_h, w, results[-1].lipschitz, statistics.median(iters),
                                             args.cpu_sample_iters)
     return line
 
@@ -300,13 +317,13 @@ def run_reference(args):
     import torch
     device = f"cuda:{local}"
     torch.cuda.set_device(local)
-    w, X, y = make_inputs(device)       # synthetic inputs only; the timed work runs on the host
+    w, X, y = make_inputs(device, args.workload)   # synthetic inputs only; the timed work runs on the host
     Xh, yh = host_copy(X, y)
     del X, y
     torch.cuda.empty_cache()
     from oracle import solver
     L = 2.0 * solver.spectral_norm_sq(Xh, iters=30) * 1.01
-    iters_to_gap = GPU_ITERS_TO_GAP.get(WORKLOAD) or args.ref_iters
+    iters_to_gap = GPU_ITERS_TO_GAP.get(args.workload) or args.ref_iters
     for _ in range(args.warmup):
         oracle_sample(Xh, yh, w, L, 1)
     t0 = time.perf_counter()
@@ -320,7 +337,8 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": w.n, "p": w.p, "gap_tol": GAP_TOL},
+            "config": {"workload": args.workload, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2,
+                       "rho": w.rho, "loss": w.loss, "M": w.M, "gap_tol": GAP_TOL, "snr": w.snr},
             "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": cpu_cores(),
                              "kind": "oracle",
                              "sample": f"each step {args.cpu_sample_iters} oracle FISTA iterations on "
@@ -333,9 +351,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic workload (ls_4000x50000_f32: the counter-capture case)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample-iters", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-iters", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -154,6 +154,9 @@ WORKLOADS = {
                                    "ls", 3.0),
     "logistic_20000x50000_f32": Workload("logistic_20000x50000_f32", 20000, 50000, 0.9,
                                          50, 0.1, "logistic", 3.0),
+    # the same recipe on a fifth of the rows (800 MB of X, still far larger than
+    # L2): the case counter captures of the fused pass run on
+    "ls_4000x50000_f32": Workload("ls_4000x50000_f32", 4000, 50000, 0.9, 50, 0.1, "ls", 3.0),
     "batch256_5000x10000_f32": Workload("batch256_5000x10000_f32", 5000, 10000, 0.7, 20,
                                         0.5, "ls", 5.0,
                                         extra={"nodes": 256, "j0_max": 40, "j1_max": 19}),
