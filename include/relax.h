@@ -156,6 +156,29 @@ relax_status prox_persp(const void* beta_in, void* beta_out, int64_t p, double s
                         int32_t k, double lambda2, double M, const int8_t* fixings,
                         int32_t dtype, int32_t* counts_out, void* stream);
 
+/* prox_persp without any allocation.  The paper has no counterpart: this is a
+ * library convenience.  Some callers cannot allocate device memory while they
+ * work: a solver embedded in a framework whose memory pool owns the whole GPU,
+ * or a node loop with a hard latency budget where an allocator call may block,
+ * synchronize or fail.  This call computes exactly what prox_persp computes
+ * (same arguments, layouts and results) but takes its scratch from one
+ * 64 KiB array in device memory that every GPU which loads the library holds
+ * until the process exits; it calls no allocation routine.
+ *   Limit: p must need at most 64 KiB of scratch (3 * 256 * 8 bytes of
+ *   accumulators + 160 bytes per block of the launch, which admits every
+ *   p <= 189440 for either dtype).  Beyond it: RELAX_ENOTSUP, with the sizes in
+ *   relax_error_detail(), and nothing is launched.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call shares the one array and leaves its contents behind (each call
+ *   zeroes what it needs at its start): calls that overlap on the GPU, e.g. on
+ *   two streams without ordering between them, race and give wrong results.
+ *   Does not synchronize. */
+relax_status prox_persp_noalloc(const void* beta_in, void* beta_out, int64_t p, double step,
+                                int32_t k, double lambda2, double M, const int8_t* fixings,
+                                int32_t dtype, int32_t* counts_out, void* stream);
+
 /* g_N(beta) (Eq. 5; value of Algorithm 1 / Thm 4.4) into out_host[0]; +inf when
  * beta is outside dom g_N (beyond a relative tolerance of 4 ulp of dtype).
  *   beta: device p of dtype.  Synchronizes `stream`. */

@@ -9,5 +9,5 @@ from .binding import (  # noqa: F401
     RELAX_F32, RELAX_F64, RELAX_BF16, RELAX_FP8E4M3, RELAX_LS, RELAX_LOGISTIC,
     RelaxError, Options, Result, Handle, load, lib_path, exported_symbols,
     relax_create, relax_solve, relax_xpass, relax_certify, relax_destroy,
-    prox_persp, gval_persp, gstar_persp, relax_strerror, relax_error_detail, STATUS,
+    prox_persp, prox_persp_noalloc, gval_persp, gstar_persp, relax_strerror, relax_error_detail, STATUS,
 )

@@ -69,6 +69,7 @@ def load():
     lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_destroy.argtypes = [vp]
     lib.prox_persp.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
+    lib.prox_persp_noalloc.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
     lib.gval_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
     lib.gstar_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
     lib.relax_strerror.argtypes = [ctypes.c_int]
@@ -190,6 +191,15 @@ def prox_persp(beta_in, beta_out, step, k, lambda2, M, fixings=None, counts_out=
                              float(lambda2), float(M), _ptr(fixings), _dtype_code(beta_in),
                              _ptr(counts_out), _stream(beta_in.device))
     _check(code, "prox_persp")
+
+
+def prox_persp_noalloc(beta_in, beta_out, step, k, lambda2, M, fixings=None, counts_out=None):
+    """prox_persp with its scratch in the library's fixed device array (no allocation)."""
+    _need_cuda(beta_in, beta_out, fixings, counts_out)
+    code = load().prox_persp_noalloc(_ptr(beta_in), _ptr(beta_out), beta_in.numel(), float(step), int(k),
+                                     float(lambda2), float(M), _ptr(fixings), _dtype_code(beta_in),
+                                     _ptr(counts_out), _stream(beta_in.device))
+    _check(code, "prox_persp_noalloc")
 
 
 def gval_persp(beta, k, M, fixings=None) -> float:

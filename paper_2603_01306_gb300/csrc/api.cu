@@ -954,3 +954,9 @@ relax_status gstar_persp(const void* alpha, int64_t p, int32_t k, double M, cons
 }
 
 }  // extern "C"
+
+// Error text for this thread's relax_error_detail(), set by other translation
+// units of the library.
+namespace relax {
+void set_error_detail(const char* msg) { snprintf(g_detail, sizeof(g_detail), "%s", msg); }
+}  // namespace relax
