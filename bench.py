@@ -261,7 +261,7 @@ def run_ours(args):
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "relaxations/s",
                 "h2d_bytes_per_step": w.n * w.p * 4 + w.n * 4, "d2h_bytes_per_step": w.p * 4,
                 "steps": e2e_steps,
-                "note": "X, y from pinned host; handle create (power iteration), solve, beta to host, destroy"},
+                "note": "X, y from pinned host; handle create (Lanczos estimate of L), solve, beta to host, destroy"},
         "clocks": clocks,
         "gpu_launches": sum(r.launches for r in results),
     }

@@ -66,7 +66,7 @@ typedef enum {
 typedef struct {
   double M;            /* box bound of Eq. 1; 0 -> 2.0; +INFINITY allowed (no box) */
   double eta;          /* restart factor of Sec. 3.4; 0 -> e^3 */
-  double lipschitz;    /* L of beta -> F(X beta); 0 -> power iteration at create */
+  double lipschitz;    /* L of beta -> F(X beta); 0 -> Lanczos estimate at create */
   int32_t max_iters;   /* 0 -> 100000 */
   int32_t precision;   /* storage used for the in-loop X reads: 0 -> dtype of X;
                           RELAX_BF16 / RELAX_FP8E4M3 require X in RELAX_F32 and make the
@@ -105,8 +105,10 @@ typedef struct {
  *      aligned the handle keeps an aligned internal copy.
  *   y: device, n elements of `dtype` (copied into the handle).
  *   k >= 1, lambda2 > 0; opt may be NULL (defaults).
- * Computes L = c_f ||X||_2^2 (c_f = 2 for LS, 1/4 for logistic) by power
- * iteration unless opt->lipschitz > 0.  Synchronizes `stream`. */
+ * Computes L = c_f ||X||_2^2 (c_f = 2 for LS, 1/4 for logistic) unless
+ * opt->lipschitz > 0: the largest Ritz value of a Lanczos run on X'X (full
+ * reorthogonalisation, deterministic reductions) plus a 1% margin.
+ * Synchronizes `stream`. */
 relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_t n,
                           int64_t p, int64_t ldx, int32_t dtype, int32_t loss, int32_t k,
                           double lambda2, const relax_options* opt, void* stream);
@@ -121,6 +123,10 @@ relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_
  *      smallest Phi seen.
  *   out: host; filled on every return path after argument validation, including
  *      RELAX_ENOTCONV / RELAX_ETIMEOUT (dual_bound stays a valid bound).
+ * The loop stops when its own gap estimate reaches gap_tol (0.7 gap_tol when X
+ * is FP32 or narrower, where that estimate is not FP64); the FP64 certificate
+ * of the best pair decides the status, and when it misses gap_tol the loop
+ * resumes with a 4x tighter target (at most 3 times).
  * Synchronizes the handle's stream. */
 relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* warm_start,
                          double gap_tol, void* beta_out, relax_result* out);

@@ -330,41 +330,161 @@ PArgs base_pargs(relax_handle* h) {
   return a;
 }
 
-// L = c_f * ||X||_2^2 by power iteration on the operator the loop uses
-relax_status power_iteration(relax_handle* h, double* L_out) {
-  double* v = (double*)h->vb[8];
-  double* w = (double*)h->vb[9];
-  const unsigned g = grid_for(h->p);
-  fill_kernel<double><<<g, 256, 0, h->stream>>>(v, h->p, 1.0 / std::sqrt((double)h->p));
-  CU(cudaGetLastError());
-  double ray_prev = 0.0, ray = 0.0;
-  for (int it = 0; it < 500; ++it) {
-    PassState ps{};
-    ps.beta = v;
-    ps.zout = h->vb[10];
-    *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;   // staging in pinned memory
-    CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-    XSArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux);
-    CU(run_pass(h, h->pl_ident, a, h->stream));
-    CU(cudaMemsetAsync(h->dscr, 0, 2 * sizeof(double), h->stream));
-    reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, h->pl_ident.Gr, 1, h->p, w, h->dscr);
-    sumsq_kernel<<<grid_for(h->n), 256, 0, h->stream>>>((const double*)h->vb[10], h->n, h->dscr + 1);
-    CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-    int dst = 0;
-    CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (dst != ST_OK) return map_dev_status(dst);
-    ray = h->h_d[1];   // ||X v||^2 with ||v|| = 1
-    scale_kernel<double><<<g, 256, 0, h->stream>>>(w, h->p, h->dscr);
-    CU(cudaGetLastError());
-    std::swap(v, w);
-    if (it > 3 && std::fabs(ray - ray_prev) <= 1e-7 * ray) break;
-    ray_prev = ray;
+// ---- Lanczos estimate of ||X||_2^2 (deterministic: fixed grids, fixed-order sums)
+constexpr int LZ_BLOCKS = 128;   // blocks of the partial dot products
+constexpr int LZ_MAX = 64;       // Lanczos steps at most
+
+// part[b][l] = sum over block b's indices of Q[l][i] * w[i], for l < m
+__global__ void mdot_partial_kernel(const double* Q, int m, const double* w, int64_t p, double* part) {
+  __shared__ double red[8];
+  for (int l = 0; l < m; ++l) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+      s += Q[(int64_t)l * p + i] * w[i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+      part[(int64_t)blockIdx.x * m + l] = t;
+    }
+    __syncthreads();
   }
-  if (!(ray > 0.0) || !std::isfinite(ray)) return RELAX_ENUMERIC;
+}
+// c[l] = sum_b part[b][l] in block order
+__global__ void mdot_final_kernel(const double* part, int nb, int m, double* c) {
+  const int l = threadIdx.x;
+  if (l < m) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * m + l];
+    c[l] = s;
+  }
+}
+// w -= sum_l c[l] Q[l]
+__global__ void msub_kernel(const double* Q, int m, const double* c, double* w, int64_t p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int l = 0; l < m; ++l) s -= c[l] * Q[(int64_t)l * p + i];
+    w[i] = s;
+  }
+}
+// q = w * scale
+__global__ void scaled_copy_kernel(const double* w, double scale, double* q, int64_t p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = w[i] * scale;
+}
+// a deterministic start vector with no special structure
+__global__ void lanczos_start_kernel(double* q, int64_t p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = 1.0 + (double)((uint64_t)(i + 1) * 2654435761ull % 1024ull) / 1024.0;
+}
+
+// largest eigenvalue of the symmetric tridiagonal matrix (a[0..m), b[1..m))
+// by Sturm-sequence bisection
+double tridiag_max_eig(const double* a, const double* b, int m) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i]) : 0.0) + (i + 1 < m ? std::fabs(b[i + 1]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double d = a[0] - x;
+    if (d < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      if (d == 0.0) d = 1e-300;
+      d = a[i] - x - b[i] * b[i] / d;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), 1e-300); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m) hi = mid;   // every eigenvalue below mid
+    else lo = mid;
+  }
+  return hi;
+}
+
+// L = c_F * ||X||_2^2: Lanczos on X'X (the operator the loop applies, in the
+// loop's storage of X) with full reorthogonalisation; the largest Ritz value
+// converges from below, so a 1% margin is added.
+relax_status power_iteration(relax_handle* h, double* L_out) {
+  const int64_t p = h->p;
+  double* w = (double*)h->vb[9];
+  double* Q = nullptr;
+  double* part = nullptr;
+  double* c = nullptr;
+  relax_status rs = RELAX_OK;
+  if ((rs = alloc((void**)&Q, (size_t)(LZ_MAX + 1) * p * sizeof(double))) != RELAX_OK) return rs;
+  if ((rs = alloc((void**)&part, (size_t)LZ_BLOCKS * (LZ_MAX + 1) * sizeof(double))) != RELAX_OK) { cudaFree(Q); return rs; }
+  if ((rs = alloc((void**)&c, (size_t)(LZ_MAX + 1) * sizeof(double))) != RELAX_OK) { cudaFree(Q); cudaFree(part); return rs; }
+  const unsigned g = grid_for(p);
+  double alpha[LZ_MAX + 1] = {}, beta[LZ_MAX + 2] = {};
+  double theta = 0.0, theta_prev = 0.0;
+  // c[0..m) = Q[0..m)' v (host copy in hc)
+  auto mdot = [&](const double* Qb, int m, const double* v, double* hc) -> cudaError_t {
+    mdot_partial_kernel<<<LZ_BLOCKS, 256, 0, h->stream>>>(Qb, m, v, p, part);
+    mdot_final_kernel<<<1, 128, 0, h->stream>>>(part, LZ_BLOCKS, m, c);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, c, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e;
+  };
+  auto run = [&]() -> relax_status {
+    lanczos_start_kernel<<<g, 256, 0, h->stream>>>(Q, p);
+    CU(cudaGetLastError());
+    double nrm2 = 0.0;
+    CU(mdot(Q, 1, Q, &nrm2));
+    scaled_copy_kernel<<<g, 256, 0, h->stream>>>(Q, 1.0 / std::sqrt(nrm2), Q, p);
+    int m = 0;
+    for (int j = 0; j < LZ_MAX; ++j) {
+      // w = X'X q_j
+      PassState ps{};
+      ps.beta = Q + (int64_t)j * p;
+      ps.zout = h->vb[10];
+      *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;   // staging in pinned memory
+      CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
+      XSArgs a = pass_args(h, h->pl_ident, LINK_IDENT, h->ps_aux);
+      CU(run_pass(h, h->pl_ident, a, h->stream));
+      reduce_partials_kernel<double, double><<<g, 256, 0, h->stream>>>(h->xg, h->pl_ident.Gr, 1, p, w, nullptr);
+      CU(cudaGetLastError());
+      // two rounds of classical Gram-Schmidt against q_0..q_j
+      double hc[LZ_MAX + 1], hc2[LZ_MAX + 1];
+      CU(mdot(Q, j + 1, w, hc));
+      msub_kernel<<<g, 256, 0, h->stream>>>(Q, j + 1, c, w, p);
+      CU(mdot(Q, j + 1, w, hc2));
+      msub_kernel<<<g, 256, 0, h->stream>>>(Q, j + 1, c, w, p);
+      CU(cudaGetLastError());
+      int dst = 0;
+      CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+      if (dst != ST_OK) return map_dev_status(dst);
+      alpha[j] = hc[j] + hc2[j];
+      double b2 = 0.0;
+      CU(mdot(w, 1, w, &b2));
+      beta[j + 1] = std::sqrt(std::max(b2, 0.0));
+      m = j + 1;
+      theta = tridiag_max_eig(alpha, beta, m);
+      if (!std::isfinite(theta)) return RELAX_ENUMERIC;
+      if (j >= 4 && std::fabs(theta - theta_prev) <= 1e-12 * theta) break;
+      if (!(beta[j + 1] > 1e-13 * std::max(theta, 1e-300))) break;   // invariant subspace found
+      theta_prev = theta;
+      scaled_copy_kernel<<<g, 256, 0, h->stream>>>(w, 1.0 / beta[j + 1], Q + (int64_t)(j + 1) * p, p);
+      CU(cudaGetLastError());
+    }
+    return RELAX_OK;
+  };
+  rs = run();
+  cudaStreamSynchronize(h->stream);
+  cudaFree(Q);
+  cudaFree(part);
+  cudaFree(c);
+  if (rs != RELAX_OK) return rs;
+  if (!(theta > 0.0) || !std::isfinite(theta)) return RELAX_ENUMERIC;
   const double cf = h->loss == RELAX_LS ? 2.0 : 0.25;
-  *L_out = cf * ray * 1.01;   // 1% margin over the Rayleigh estimate of ||X||^2
+  *L_out = cf * theta * 1.01;   // 1% margin over the Ritz estimate of ||X||^2
   return RELAX_OK;
 }
 
@@ -635,7 +755,10 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.psi_best = -INFINITY;
   s.kbar = h->k - j1;
   s.pbar = jf;
-  s.tol = gap_tol;
+  // With FP32 (or narrower) X the loop's gap is an estimate: aim a little below
+  // gap_tol so that the FP64 certificate of the final pair usually confirms it
+  // at once.  With FP64 X the loop's gap is the certificate's, to rounding.
+  s.tol = (h->dtype == RELAX_F64 && h->xk_loop == XK_F64) ? gap_tol : 0.7 * gap_tol;
   s.ps.beta = s.beta_cur;
   s.ps.zout = s.z_cur;
   s.ps.zprev = s.z_prev;

@@ -163,3 +163,28 @@ def test_invalid_node_rejected(lib):
     fix = np.array([1, 1, 0, 0, 0, 0], dtype=np.int8)     # |J1| = 2 > k = 1
     with pytest.raises(lib.RelaxError):
         gpu_solve(lib, X, y, "ls", 1, 0.3, 1.0, 1.0, fix=fix)
+
+
+def test_solve_is_deterministic(lib):
+    """Two handles on the same data (L estimated on the device each time) give
+    bit-identical L, iteration counts, bounds and beta: every reduction on the
+    path sums in a fixed order."""
+    w = synth.Workload("det", 600, 3000, 0.8, 12, 0.3, "ls")
+    X, y = problem(w, dtype=np.float32)
+    Xd = torch.tensor(X, device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    runs = []
+    for _ in range(2):
+        h = lib.Handle(Xd, yd, loss="ls", k=w.k, lambda2=w.lambda2, M=w.M)
+        beta, res, code = h.solve(gap_tol=1e-6)
+        runs.append((beta.cpu().numpy().copy(), res, code))
+        h.close()
+    (b0, r0, c0), (b1, r1, c1) = runs
+    assert c0 == c1 == 0
+    assert r0.lipschitz == r1.lipschitz
+    assert r0.iters == r1.iters and r0.restarts == r1.restarts
+    assert r0.dual_bound == r1.dual_bound and r0.primal == r1.primal
+    assert np.array_equal(b0, b1)
+    # the Lanczos estimate is within its 1% margin above ||X||^2 (times 2 for LS)
+    lam = np.linalg.norm(X.astype(np.float64), 2) ** 2
+    assert 2 * lam * 0.999 <= r0.lipschitz <= 2 * lam * 1.0101
