@@ -229,10 +229,11 @@ struct relax_handle {
   XSPlan pl_loop, pl_cert, pl_certz, pl_ident;
   PPlan pp_iter, pp_eval;
   // buffers
-  double* xpart = nullptr;       // [Gc][n][NF] strip partials of the pass
   double* xg = nullptr;          // [Gr][2][p] X' r per row group
   double* lterm = nullptr;       // [n][2] certification loss terms
-  unsigned* xcnt = nullptr;      // pass block counters cnt[nblk]
+  unsigned* xcnt = nullptr;      // per-pass zeroed area: block counters, max |beta|, fixed-point z
+  double rowl1_x = 0.0;          // max_i ||x_i||_1 of X (NaN if X holds a NaN)
+  double rowl1_q = 0.0;          // the same for the BF16/FP8 copy (stored values)
   IterState* st = nullptr;
   PassState* ps_aux = nullptr;
   void* vb[13] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
@@ -258,7 +259,7 @@ void handle_free(relax_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xpart, h->xg, h->lterm, h->xcnt, h->st,
+  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xg, h->lterm, h->xcnt, h->st,
                   h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (void* q : h->vb) if (q) cudaFree(q);
@@ -296,10 +297,10 @@ XSArgs pass_args(relax_handle* h, const XSPlan& pl, int link, PassState* ps) {
   a.y = (const double*)h->y;
   a.colscale = lowp ? h->colscale : nullptr;
   a.ps = ps;
-  a.part = h->xpart;
   a.g = h->xg;
   a.lterm = nullptr;
-  a.cnt = h->xcnt;
+  a.rowl1 = lowp ? h->rowl1_q : h->rowl1_x;
+  xstrip_zero_layout(pl, h->xcnt, a);
   a.status = h->status;
   a.limit_ns = h->limit_ns;
   return a;
@@ -328,6 +329,54 @@ PArgs base_pargs(relax_handle* h) {
   a.status = h->status;
   a.limit_ns = h->limit_ns;
   return a;
+}
+
+// ---- max_i ||x_i||_1 (bound of every dot product a pass forms, with max |beta|)
+__device__ __forceinline__ double abs_of(double v) { return fabs(v); }
+__device__ __forceinline__ double abs_of(float v) { return fabs((double)v); }
+__device__ __forceinline__ double abs_of(__nv_bfloat16 v) { return fabs((double)__bfloat162float(v)); }
+__device__ __forceinline__ double abs_of(__nv_fp8_e4m3 v) { return fabs((double)(float)v); }
+
+// one warp per row; FP64 sums; a NaN anywhere makes the result NaN (its bits
+// compare above those of every finite value and of +Inf)
+template <typename T>
+__global__ void rowl1_kernel(const T* X, int64_t n, int64_t p, int64_t ld, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long mb = 0ull;
+  for (int64_t i = w0; i < n; i += nw) {
+    double sum = 0.0;
+    for (int64_t j = lane; j < p; j += 32) sum += abs_of(X[i * ld + j]);
+    sum = warp_sum(sum);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(sum);
+    mb = bits > mb ? bits : mb;
+  }
+  if (lane == 0 && mb) atomicMax(out, mb);
+}
+
+template <typename T>
+relax_status row_l1(const void* X, int64_t n, int64_t p, int64_t ld, cudaStream_t st, double* out) {
+  unsigned long long* d = nullptr;
+  relax_status rs = alloc((void**)&d, sizeof(unsigned long long));
+  if (rs != RELAX_OK) return rs;
+  unsigned long long hb = 0ull;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    rowl1_kernel<T><<<1024, 256, 0, st>>>(static_cast<const T*>(X), n, p, ld, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, d, sizeof(hb), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_detail("row_l1", e, __LINE__);
+    return map_cuda(e);
+  }
+  double v;
+  std::memcpy(&v, &hb, sizeof(v));
+  *out = v;
+  return RELAX_OK;
 }
 
 // ---- Lanczos estimate of ||X||_2^2 (deterministic: fixed grids, fixed-order sums)
@@ -662,6 +711,10 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       TRYC(xstrip_bind(h->pl_ident, xl, ldl, n, p));
       TRYC(xstrip_bind(h->pl_cert, h->X, h->ldx, n, p));
       TRYC(xstrip_bind(h->pl_certz, h->X, h->ldx, n, p));
+      if (dtype == RELAX_F64) TRY(row_l1<double>(h->X, n, p, h->ldx, h->stream, &h->rowl1_x));
+      else TRY(row_l1<float>(h->X, n, p, h->ldx, h->stream, &h->rowl1_x));
+      if (h->xk_loop == XK_BF16) TRY(row_l1<__nv_bfloat16>(h->Xq, n, p, h->ldq, h->stream, &h->rowl1_q));
+      if (h->xk_loop == XK_FP8) TRY(row_l1<__nv_fp8_e4m3>(h->Xq, n, p, h->ldq, h->stream, &h->rowl1_q));
     }
     if (std::getenv("RELAX_DEBUG")) {
       const XSPlan& q = h->pl_loop;
@@ -672,17 +725,15 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(pphase_plan(h->pp_eval, true, p));
     {
       const XSPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
-      size_t part_n = 0;
-      int nblk_max = 0, gr_max = 1;
+      size_t zero_b = 0;
+      int gr_max = 1;
       for (const XSPlan* q : pls) {
-        part_n = std::max(part_n, (size_t)n * q->Gc * q->NF);
+        zero_b = std::max(zero_b, xstrip_zero_bytes(*q, n));
         gr_max = std::max(gr_max, q->Gr);
-        nblk_max = std::max(nblk_max, q->nblk);
       }
-      TRY(alloc((void**)&h->xpart, part_n * sizeof(double)));
       TRY(alloc((void**)&h->xg, (size_t)gr_max * 2 * p * sizeof(double)));
       TRY(alloc((void**)&h->lterm, (size_t)2 * n * sizeof(double)));
-      TRY(alloc((void**)&h->xcnt, (size_t)nblk_max * sizeof(unsigned)));
+      TRY(alloc((void**)&h->xcnt, zero_b));
     }
     TRY(alloc((void**)&h->st, sizeof(IterState)));
     TRY(alloc((void**)&h->ps_aux, sizeof(PassState)));

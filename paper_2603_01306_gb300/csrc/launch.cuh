@@ -32,7 +32,10 @@ struct XSPlan {
 cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p);
 // encode the plan's tensor map of X (16-byte aligned, ldx * size a multiple of 16)
 cudaError_t xstrip_bind(XSPlan& pl, const void* X, int64_t ldx, int64_t n, int64_t p);
-// the block counters (nblk unsigned at a.cnt) are zeroed on the stream before the launch
+// The per-pass area (block counters, the grid's max |beta|, z in fixed point)
+// starts at a.cnt; xstrip_launch zeroes it on the stream before the launch.
+size_t xstrip_zero_bytes(const XSPlan& pl, int64_t n);
+void xstrip_zero_layout(const XSPlan& pl, void* base, XSArgs& a);   // sets a.cnt, a.zcnt, a.zmax, a.zfix
 cudaError_t xstrip_launch(const XSPlan& pl, const XSArgs& a, cudaStream_t st);
 
 struct PPlan {

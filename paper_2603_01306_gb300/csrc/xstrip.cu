@@ -157,8 +157,23 @@ cudaError_t xstrip_bind(XSPlan& pl, const void* X, int64_t ldx, int64_t n, int64
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The per-pass area zeroed before every launch:
+//   cnt[nblk] | zcnt | zmax[2] | zfix[NF][n]
+static size_t zero_off_zcnt(const XSPlan& pl) { return ((size_t)pl.nblk * sizeof(unsigned) + 15) / 16 * 16; }
+size_t xstrip_zero_bytes(const XSPlan& pl, int64_t n) {
+  return zero_off_zcnt(pl) + 32 + (size_t)pl.NF * n * sizeof(unsigned long long);
+}
+void xstrip_zero_layout(const XSPlan& pl, void* base, XSArgs& a) {
+  unsigned char* b = static_cast<unsigned char*>(base);
+  const size_t oz = zero_off_zcnt(pl);
+  a.cnt = reinterpret_cast<unsigned*>(b);
+  a.zcnt = reinterpret_cast<unsigned*>(b + oz);
+  a.zmax = reinterpret_cast<unsigned long long*>(b + oz + 16);
+  a.zfix = reinterpret_cast<unsigned long long*>(b + oz + 32);
+}
+
 cudaError_t xstrip_launch(const XSPlan& pl, const XSArgs& a, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(a.cnt, 0, sizeof(unsigned) * (size_t)pl.nblk, st);
+  cudaError_t e = cudaMemsetAsync(a.cnt, 0, xstrip_zero_bytes(pl, a.n), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

@@ -17,19 +17,27 @@
 //    lane 16 of warp 0 loads the same tiles again, from L2, into ring B (SB
 //    stages);
 //  * SA "dot" warps (warp a owns stage a of ring A): per row the strip's partial
-//    dot product with beta, stored to part[cc][row], then counted in cnt[b];
+//    dot product with beta, added to the row's z in 64-bit fixed point
+//    (integer additions commute, so z does not depend on the arrival order of
+//    the Gc strips), then the block is counted in cnt[b];
 //  * SB "axpy" warps (warp e owns stage e of ring B): once cnt[b] = Gc each
-//    sums the Gc partials of every row of the block in a fixed order (so every
-//    CTA gets the same z, whatever the arrival order), applies the link and
-//    accumulates X' r over its strip; CTA (k mod Gc) of the row group records
-//    z and the loss terms of the group's k-th block; at the end the axpy warps'
-//    strip sums are combined in a fixed order into g[cr][q][strip].
+//    reads z of the block's rows, applies the link and accumulates X' r over
+//    its strip; CTA (k mod Gc) of the row group records z and the loss terms
+//    of the group's k-th block; at the end the axpy warps' strip sums are
+//    combined in a fixed order into g[cr][q][strip].
+// Fixed point: z = Z * 2^-S with S chosen per pass from a bound of every
+// partial and of their sum, max_i ||x_i||_1 * max_j |beta_j| < 2^(61-S); the
+// grid agrees on max_j |beta_j| through one atomic max and a counter, which the
+// dot warps wait for only before their first addition (the HBM stream starts
+// at once).
 // Each stage has exactly one consumer warp, which therefore never waits on a
 // barrier phase more than one ahead of the last one it saw.  Phase A may lead
 // phase B by at most `lag` blocks of the CTA (L2 footprint).  Every wait is
 // bounded: on expiry the kernel records ST_TIMEOUT, stops issuing and waiting,
 // lets the copies in flight land and returns.
 #pragma once
+#include <climits>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -60,7 +68,10 @@ struct XSArgs {
   const double* y;
   const float* colscale;
   PassState* ps;
-  double* part;          // [Gc][n][NF] strip partials (FP32 pair bits or FP64)
+  unsigned long long* zfix;   // [NF][n] z in fixed point (two's complement)   } zeroed
+  unsigned long long* zmax;   // [NF] max_j |beta_j| (bits of a nonnegative double) } before
+  unsigned* zcnt;             // CTAs that have added to zmax                   } the launch
+  double rowl1;               // max_i ||x_i||_1 of the stored X (NaN when X holds a NaN)
   double* g;             // [Gr][NB][p] X' r per row group
   double* lterm;         // [n][2] per-row {F, -F*(-zeta)} (certification links) or NULL
   unsigned* cnt;         // [nblk] CTAs done with the block's dots (zeroed before the launch)
@@ -126,6 +137,17 @@ __device__ __forceinline__ uint64_t policy_evict_normal() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
   return p;
+}
+
+// Scale exponent of the fixed-point z for the bound `bz` of every partial and
+// of their sum: |value| * 2^S < 2^61.  INT_MIN marks a bound that is not
+// finite (NaN or Inf in X or beta): z is then NaN.
+__device__ __forceinline__ int fixed_scale(double bz) {
+  if (!(bz < INFINITY)) return INT_MIN;
+  if (bz == 0.0) return 0;
+  int e = 0;
+  frexp(bz, &e);   // bz < 2^e
+  return max(-1000, min(1000, 61 - e));
 }
 
 // (h, l) += (rh, rl) for compensated FP32 pairs
@@ -333,6 +355,32 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           bv[f][t][l] = in ? (TA)(static_cast<const double*>(f == 0 ? a.ps->beta : a.ps->beta2)[col] * sc) : (TA)0;
       }
     }
+    if (st == 0) {
+      // this CTA's max |beta_j| (NaN dominates: its bits compare above +Inf)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        unsigned long long mb = 0ull;
+#pragma unroll
+        for (int t = 0; t < TV; ++t)
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)bv[f][t][l]));
+            mb = bits > mb ? bits : mb;
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long other = __shfl_xor_sync(0xffffffffu, mb, o);
+          mb = other > mb ? other : mb;
+        }
+        if (lane == 0) atomicMax(&a.zmax[f], mb);
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(a.zcnt, 1u);
+    }
+    int zs[NF];          // fixed-point exponents, known after the first block's dots
+    double zf[NF];       // 2^zs
+    bool have_scale = false;
     for (int k = st; k < kloc; k += a.SA) {
       if (tmo) break;
       if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullA[st], (k / a.SA) & 1, a.limit_ns, a.status))) {
@@ -362,7 +410,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
             for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
         }
       }
-      double mine[NF];   // lane 2j: the strip partial of row j
+      // lane 2j: the strip partial of row j, as (hi, lo)
+      TA mh[NF], ml[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         if constexpr (kF32) {
@@ -370,17 +419,36 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
           for (int jj = 0; jj < XS_MAXB; ++jj) pl[jj] = 0.f;
           butterfly16(ph[f], pl, lane);
-          mine[f] = pack_pair(ph[f][0], pl[0]);
+          mh[f] = ph[f][0];
+          ml[f] = pl[0];
         } else {
           butterfly16(ph[f], lane);
-          mine[f] = ph[f][0];
+          mh[f] = ph[f][0];
+          ml[f] = (TA)0;
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyA[st]);   // stage free: the rest works on registers
+      if (!have_scale) {
+        // every CTA's max |beta_j| is in: the common scale of this pass
+        if (!__all_sync(0xffffffffu, wait_count(a.zcnt, gridDim.x, a.limit_ns, a.status))) {
+          tmo = 1;
+          break;
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          zs[f] = fixed_scale(a.rowl1 * __longlong_as_double((long long)__ldcg(&a.zmax[f])));
+          zf[f] = zs[f] == INT_MIN ? 0.0 : ldexp(1.0, zs[f]);
+        }
+        have_scale = true;
+      }
       if ((lane & 1) == 0 && (lane >> 1) < rows) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) a.part[((size_t)cc * n + r0 + (lane >> 1)) * NF + f] = mine[f];
+        for (int f = 0; f < NF; ++f) {
+          if (zs[f] == INT_MIN) continue;
+          const long long q = __double2ll_rn((double)mh[f] * zf[f]) + __double2ll_rn((double)ml[f] * zf[f]);
+          atomicAdd(&a.zfix[(size_t)f * n + r0 + (lane >> 1)], (unsigned long long)q);
+        }
       }
       __threadfence();
       __syncwarp();
@@ -402,9 +470,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
     const double* zprev = static_cast<const double*>(a.ps->zprev);
     double* zout = static_cast<double*>(a.ps->zout);
     const double mom = a.ps->mom;
-    // lane = 16 hb + j: row j of the block, strips cc = 2i + hb
-    const int jl = lane & 15, hb = lane >> 4;
-    const int npl = (a.Gc - hb + 1) / 2;   // strips this lane sums
+    const int jl = lane & 15, hb = lane >> 4;   // the block row this lane evaluates (hb: duplicate)
+    double zinv[NF];
+    bool have_scale = false;
     for (int k = st; k < kloc; k += a.SB) {
       if (tmo) break;
       const int b = cr + k * a.Gr;
@@ -417,40 +485,17 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         tmo = 1;
         break;
       }
-      // z of row j: the Gc strip partials in a fixed order (even strips, odd
-      // strips, then even + odd), identical in every CTA
+      if (!have_scale) {   // final once any block is complete
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const int zs = fixed_scale(a.rowl1 * __longlong_as_double((long long)__ldcg(&a.zmax[f])));
+          zinv[f] = zs == INT_MIN ? __longlong_as_double(0x7ff8000000000000ll) : ldexp(1.0, -zs);
+        }
+        have_scale = true;
+      }
       double z[NF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const double* pr = a.part + ((size_t)hb * n + rowj) * NF + f;
-        const size_t step = (size_t)2 * n * NF;
-        constexpr int U = 20;
-        if constexpr (kF32) {
-          float h = 0.f, l = 0.f;
-          for (int i0 = 0; i0 < npl; i0 += U) {
-            double v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = (i0 + u < npl) ? __ldcg(pr + (size_t)(i0 + u) * step) : 0.0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) add_pair(h, l, v[u]);
-          }
-          const float oh = __shfl_xor_sync(0xffffffffu, h, 16), ol = __shfl_xor_sync(0xffffffffu, l, 16);
-          float eh = hb ? oh : h, el = hb ? ol : l;   // even strips' sum first
-          pair_add(eh, el, hb ? h : oh, hb ? l : ol);
-          z[f] = (double)eh + (double)el;
-        } else {
-          double sum = 0.0;
-          for (int i0 = 0; i0 < npl; i0 += U) {
-            double v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = (i0 + u < npl) ? __ldcg(pr + (size_t)(i0 + u) * step) : 0.0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) sum += v[u];
-          }
-          const double other = __shfl_xor_sync(0xffffffffu, sum, 16);
-          z[f] = hb ? other + sum : sum + other;
-        }
-      }
+      for (int f = 0; f < NF; ++f) z[f] = (double)(long long)__ldcg(&a.zfix[(size_t)f * n + rowj]) * zinv[f];
       double rv[NB], lf, ld;
       link_of<NF, NB>(a.link, z, yd, zp, mom, rv, lf, ld);
       if (jl >= rows) {
