@@ -46,7 +46,7 @@ typedef enum { RELAX_LS = 0, RELAX_LOGISTIC = 1 } relax_loss;
 typedef enum {
   RELAX_F64 = 0,     /* double */
   RELAX_F32 = 1,     /* float */
-  RELAX_BF16 = 2,    /* bfloat16 storage of X, per-column FP32 scales, FP32 accumulation */
+  RELAX_BF16 = 2,    /* bfloat16 storage of X (FP32's exponent range: no scales), FP32 accumulation */
   RELAX_FP8E4M3 = 3  /* fp8 e4m3 storage of X, per-column FP32 scales, FP32 accumulation */
 } relax_dtype;
 
@@ -70,7 +70,8 @@ typedef struct {
   int32_t max_iters;   /* 0 -> 100000 */
   int32_t precision;   /* storage used for the in-loop X reads: 0 -> dtype of X;
                           RELAX_BF16 / RELAX_FP8E4M3 require X in RELAX_F32 and make the
-                          handle keep a quantized copy (Sec. "precision" of the design) */
+                          handle keep a quantized copy that the loop reads; the FP64
+                          certificate of each solve reads the FP32 X */
   int32_t watchdog_ms; /* bound on any device-side wait; 0 -> 4000 */
   int32_t no_certify;  /* 0 -> final FP64 evaluation of the bounds with the full X */
   int32_t chunk;       /* iterations enqueued per host poll; 0 -> 32 */
@@ -124,9 +125,14 @@ relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_
  *   out: host; filled on every return path after argument validation, including
  *      RELAX_ENOTCONV / RELAX_ETIMEOUT (dual_bound stays a valid bound).
  * The loop stops when its own gap estimate reaches gap_tol (0.7 gap_tol when X
- * is FP32 or narrower, where that estimate is not FP64); the FP64 certificate
- * of the best pair decides the status, and when it misses gap_tol the loop
- * resumes with a 4x tighter target (at most 3 times).
+ * is FP32 or narrower, where that estimate is not FP64).  The FP64
+ * certificate then evaluates Phi at the best primal iterate and Psi at two
+ * dual points (the loop's best one, and zeta = -grad F(X beta_best) formed in
+ * FP64) and keeps the better bound; it decides the status.  When it misses
+ * gap_tol the loop resumes with a 4x tighter target for at most half as many
+ * iterations again, at most 3 times and only while the certified gap keeps
+ * shrinking; with BF16/FP8 storage it does not resume (that gap is the
+ * quantisation's, reported through RELAX_ENOTCONV with a valid bound).
  * Synchronizes the handle's stream. */
 relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* warm_start,
                          double gap_tol, void* beta_out, relax_result* out);

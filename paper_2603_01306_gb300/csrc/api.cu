@@ -883,10 +883,10 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   std::vector<float> xms, pms;   // per launched iteration of the current run (timing mode)
   double xms_work = 0.0, pms_work = 0.0;
   int passes_work = 0;
-  auto run_loop = [&]() {
+  auto run_loop = [&](int64_t chunk_budget) {
     xms.clear();
     pms.clear();
-    for (int64_t c = 0; c < max_chunks; ++c) {
+    for (int64_t c = 0; c < chunk_budget; ++c) {
       err = enqueue_chunk();
       if (err != cudaSuccess) break;
       ++nchunks;
@@ -917,13 +917,19 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     passes_work += it_after - it_before + 1;
   };
   int it_before = 0;
-  run_loop();
+  run_loop(max_chunks);
   // The loop's gap is tracked in the working precision; when the FP64
   // certificate of the final pair misses gap_tol, continue with a tighter
   // internal tolerance (at most 3 times).
+  // Two valid dual points are certified and the better bound is kept: the
+  // loop's best dual point (its own z) and zeta = -grad F(X beta_best) with X
+  // and the product in FP64.  A resumed run gets at most half as many
+  // iterations again, and resuming stops once it no longer helps (and never
+  // starts when X is stored in BF16/FP8: that gap is the quantisation's).
   int cert_rounds = 0;
-  double cert_primal = 0.0, cert_dual = 0.0;
+  double cert_primal = 0.0, cert_dual = 0.0, prev_crel = INFINITY;
   bool have_cert = false;
+  const bool quantized = h->xk_loop == XK_BF16 || h->xk_loop == XK_FP8;
   for (;;) {
     if (err != cudaSuccess) break;
     CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
@@ -934,12 +940,20 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     const IterState& S0 = *h->h_state;
     rs = certify(h, fixings, S0.beta_best, nullptr, S0.z_dbest);
     if (rs != RELAX_OK) return rs;
-    out->launches += 2;
+    const double phi = h->h_d[0];
+    double psi = h->h_d[1];
+    rs = certify(h, fixings, S0.beta_best, S0.beta_best, nullptr);
+    if (rs != RELAX_OK) return rs;
+    if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
+    out->launches += 4;
     have_cert = true;
-    cert_primal = h->h_d[0];
-    cert_dual = h->h_d[1];
+    cert_primal = phi;
+    cert_dual = psi;
     const double crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
-    if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel)) break;
+    if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel) || quantized ||
+        crel > 0.9 * prev_crel)
+      break;
+    prev_crel = crel;
     ++cert_rounds;
     double tol_new = S0.tol * 0.25;
     int zero = 0;
@@ -948,7 +962,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     CU(cudaMemcpyAsync(&h->st->ps.done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     it_before = S0.iter;
-    run_loop();
+    run_loop(std::max<int64_t>(8, (int64_t)S0.iter / (2 * chunk) + 1));
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);

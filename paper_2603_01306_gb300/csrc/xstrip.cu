@@ -1,5 +1,6 @@
 // Instantiations, plan and launch of the strip-stationary fused pass.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdint>
 #include <cstdlib>
@@ -34,8 +35,9 @@ static const void* xstrip_ptr(int xk, bool f64acc, int NF, int NB) {
 static int xs_tv(int vec) { return vec == 2 ? 6 : vec == 4 ? 6 : vec == 8 ? 3 : 2; }   // XSShape<VEC>::TV
 
 // Shape of the pass for an n x p design.
-//  * strips of about 2.6 KB of a row, at most 32*TV vectors (the registers of
-//    one lane row); Gc strips, Gr = SMs / Gc row groups;
+//  * strips of a row of at most 32*TV vectors (the registers of one lane
+//    row), chosen to keep the most SMs busy (Gc strips x Gr row groups), at
+//    least 2 KB wide where possible;
 //  * a strip is nbox tensor boxes of `inner` <= 256 columns;
 //  * blocks of B <= 16 rows so that a stage is about 40 KB; 3 + 3 (or 3 + 4)
 //    stages;
@@ -58,14 +60,25 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   int B_f = 0, SA_f = 0, SB_f = 0, lag_f = 0, vps_f = 0;
   if (const char* ov = std::getenv("RELAX_XS"))
     std::sscanf(ov, "%d,%d,%d,%d,%d", &B_f, &SA_f, &SB_f, &lag_f, &vps_f);
-  // strips
+  // strips: over the number of row groups Gr, the strip width (at most `cap`
+  // vectors) that keeps the most SMs busy, strips under 2 KB counted as
+  // streaming less efficiently
   const int64_t nvec = (p + vec - 1) / vec;
   const int64_t cap = (int64_t)32 * xs_tv(vec);
-  int64_t vps = std::max<int64_t>((nvec + nsm - 1) / nsm, std::min<int64_t>(166, nvec));
+  int64_t vps = 0;
+  double best = -1.0;
+  for (int64_t gr = 1; gr <= nsm; ++gr) {
+    int64_t gc = std::min<int64_t>(nsm / gr, nvec);
+    if (gc < 1) break;
+    const int64_t v = (nvec + gc - 1) / gc;
+    if (v > cap) continue;
+    gc = (nvec + v - 1) / v;
+    if (gr > 1 && n < gr * 16) break;   // too few rows to keep the groups busy
+    const double score = (double)(gc * gr) * std::sqrt(std::min(1.0, (double)(v * 16) / 2048.0));
+    if (score > best * 1.0001) { best = score; vps = v; }
+  }
   if (vps_f > 0) vps = vps_f;
-  if (vps > cap) return cudaErrorNotSupported;   // p wider than nsm strips of one lane row
-  int64_t Gc = (nvec + vps - 1) / vps;
-  vps = (nvec + Gc - 1) / Gc;                     // balance the strips
+  if (vps <= 0 || vps > cap) return cudaErrorNotSupported;   // p wider than nsm strips of one lane row
   const int64_t cols = vps * vec;
   const int64_t nbox = (cols + 255) / 256;
   const int64_t inner = ((cols + nbox - 1) / nbox + vec - 1) / vec * vec;
@@ -73,7 +86,7 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   pl.nbox = (int)nbox;
   pl.sw = nbox * inner;
   if (pl.sw / vec > cap) return cudaErrorNotSupported;
-  Gc = (p + pl.sw - 1) / pl.sw;
+  const int64_t Gc = (p + pl.sw - 1) / pl.sw;
   pl.Gc = (int)Gc;
   // blocks
   int64_t B = std::max<int64_t>(1, std::min<int64_t>(XS_MAXB, 40960 / (pl.sw * es)));
