@@ -78,7 +78,10 @@ typedef struct {
   int32_t timing;      /* 1 -> time every loop kernel with CUDA events on the handle's
                           stream (fills xpass_ms / pphase_ms of relax_result); the host
                           then waits for each chunk before enqueueing the next */
-  int32_t reserved[6];
+  int32_t stall_window; /* stall rule: the loop stops once its best duality gap has not
+                          fallen by 10% over the last quarter of its iterations and over
+                          at least this many; 0 -> 1000, < 0 -> off */
+  int32_t reserved[5];
 } relax_options;
 
 typedef struct {
@@ -97,6 +100,9 @@ typedef struct {
   int32_t xpass_count; /* fused X-passes that did work (iters + 1) */
   double xpass_ms;     /* options.timing: summed device time of those X-passes */
   double pphase_ms;    /* options.timing: summed device time of the p-phase launches */
+  int32_t stalled;     /* 1: the loop stopped on the stall rule (see stall_window) */
+  int32_t polish_iters; /* relax_solve_batch: iterations of the single-node finish that a
+                          node stalled in the batch received (0: none) */
 } relax_result;
 
 /* Create a solver handle bound to one design X and response y (Sec. 2.3).
@@ -136,6 +142,27 @@ relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_
  * Synchronizes the handle's stream. */
 relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* warm_start,
                          double gap_tol, void* beta_out, relax_result* out);
+
+/* Solve nb node relaxations of the handle's design together: the batched
+ * form of relax_solve for the nodes of one branch-and-bound tree, which all
+ * share X (Sec. 2.3 node sets; FISTA with gap restart, Sec. 3.4, per node).
+ *   fixings: device int8[nb][p] (row j: node j's J0/Jf/J1 as in relax_solve),
+ *      or NULL (every node the root).
+ *   warm_start: device [nb][p] of the handle's dtype, or NULL (zero).
+ *   beta_out: device [nb][p] of the handle's dtype: each node's best primal point.
+ *   out: host relax_result[nb], filled per node.
+ * Per iteration the active nodes' points are the columns of a matrix B;
+ * Z = X B and G = X' R run as two GEMMs (FP32 X: FP32 emulated on the BF16
+ * tensor cores; FP64 X: FP64), and each node's prox / g / g* / gap / restart
+ * step runs in its own segment of one launch.  Nodes converge after uneven
+ * iteration counts and leave the batch every 16 iterations.  Each node's bound
+ * is certified in FP64 as in relax_solve (without resuming).  Needs FP32 or
+ * FP64 storage of X (RELAX_ENOTSUP for BF16/FP8).  Returns RELAX_OK when every
+ * node certified gap_tol, else the first failing node's status (out[j].status
+ * holds each node's).  Synchronizes the handle's stream. */
+relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixings,
+                               const void* warm_start, double gap_tol, void* beta_out,
+                               relax_result* out);
 
 /* One fused pass over X (the matrix-vector products of Sec. 5.2.3 that dominate
  * the method): z = X beta, r = grad F(z), g = X' r, read of X once.

@@ -30,7 +30,7 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("watchdog_ms", ctypes.c_int32), ("no_certify", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("stall_window", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Result(ctypes.Structure):
@@ -39,7 +39,8 @@ class Result(ctypes.Structure):
                 ("dual_loop", ctypes.c_double), ("lipschitz", ctypes.c_double),
                 ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("n_nz", ctypes.c_int32), ("launches", ctypes.c_int32), ("xpass_count", ctypes.c_int32),
-                ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double)]
+                ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double),
+                ("stalled", ctypes.c_int32), ("polish_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -66,6 +67,7 @@ def load():
                                  ctypes.POINTER(Options), vp]
     lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
     lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
     lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_destroy.argtypes = [vp]
     lib.prox_persp.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
@@ -127,7 +129,7 @@ def _need_cuda(*ts):
 
 
 def make_options(M=2.0, eta=0.0, lipschitz=0.0, max_iters=0, precision=0, watchdog_ms=0,
-                 certify=True, chunk=0, timing=False) -> Options:
+                 certify=True, chunk=0, timing=False, stall_window=0) -> Options:
     o = Options()
     o.M = float(M)
     o.eta = float(eta)
@@ -138,6 +140,7 @@ def make_options(M=2.0, eta=0.0, lipschitz=0.0, max_iters=0, precision=0, watchd
     o.no_certify = 0 if certify else 1
     o.chunk = int(chunk)
     o.timing = 1 if timing else 0
+    o.stall_window = int(stall_window)
     return o
 
 
@@ -224,31 +227,73 @@ class Handle:
     """Owns a relax_handle; X and y must outlive it."""
 
     def __init__(self, X, y, loss="ls", k=10, lambda2=1.0, M=2.0, eta=0.0, lipschitz=0.0,
-                 max_iters=0, precision=0, certify=True, chunk=0, watchdog_ms=0, timing=False):
+                 max_iters=0, precision=0, certify=True, chunk=0, watchdog_ms=0, timing=False,
+                 stall_window=0):
         self.loss = {"ls": RELAX_LS, "logistic": RELAX_LOGISTIC}[loss] if isinstance(loss, str) else loss
         self.X, self.y = X, y
         self.n, self.p = X.shape
         self.dtype = X.dtype
         self.opts = make_options(M=M, eta=eta, lipschitz=lipschitz, max_iters=max_iters,
                                  precision=precision, watchdog_ms=watchdog_ms, certify=certify,
-                                 chunk=chunk, timing=timing)
+                                 chunk=chunk, timing=timing, stall_window=stall_window)
         self.h = relax_create(X, y, self.loss, k, lambda2, self.opts)
+
+    def _vec(self, t, what, rows=None, dtype=None):
+        """The C ABI takes bare pointers: check what it cannot (element type,
+        length, contiguity) before a buffer is handed over."""
+        if t is None:
+            return
+        import torch
+        want = self.dtype if dtype is None else dtype
+        shape = (self.p,) if rows is None else (rows, self.p)
+        if t.dtype != want:
+            raise TypeError(f"{what}: dtype {t.dtype}, expected {want}")
+        if tuple(t.shape) != shape and not (rows is None and t.numel() == self.p):
+            raise ValueError(f"{what}: shape {tuple(t.shape)}, expected {shape}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: must be contiguous")
 
     def solve(self, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
         import torch
         if beta_out is None:
             beta_out = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
+        self._vec(fixings, "fixings", dtype=torch.int8)
+        self._vec(warm_start, "warm_start")
+        self._vec(beta_out, "beta_out")
         code, res = relax_solve(self.h, fixings, warm_start, gap_tol, beta_out)
         return beta_out, res, code
 
+    def solve_batch(self, nb, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
+        """relax_solve_batch: nb node relaxations sharing X.  fixings: (nb, p)
+        int8 device tensor or None; warm_start: (nb, p) or None.  Returns
+        (beta (nb, p), [Result per node], status code)."""
+        import torch
+        _need_cuda(fixings, warm_start)
+        if beta_out is None:
+            beta_out = torch.empty((nb, self.p), dtype=self.dtype, device=self.X.device)
+        self._vec(fixings, "fixings", rows=nb, dtype=torch.int8)
+        self._vec(warm_start, "warm_start", rows=nb)
+        self._vec(beta_out, "beta_out", rows=nb)
+        res = (Result * nb)()
+        code = load().relax_solve_batch(self.h, int(nb), _ptr(fixings), _ptr(warm_start), float(gap_tol),
+                                        _ptr(beta_out), res)
+        if code not in (0, 4):
+            _check(code, "relax_solve_batch")
+        return beta_out, list(res), code
+
     def xpass(self, beta):
         import torch
+        self._vec(beta, "beta")
         z = torch.empty(self.n, dtype=self.dtype, device=self.X.device)
         g = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
         loss = relax_xpass(self.h, beta, z, g)
         return z, g, loss
 
     def certify(self, beta_primal, beta_dual=None, fixings=None):
+        import torch
+        self._vec(beta_primal, "beta_primal")
+        self._vec(beta_dual, "beta_dual")
+        self._vec(fixings, "fixings", dtype=torch.int8)
         return relax_certify(self.h, fixings, beta_primal,
                              beta_primal if beta_dual is None else beta_dual)
 

@@ -46,10 +46,10 @@ def _compile(src: str, obj: str, incs: list[str], extra: list[str], deps: list[s
     return obj
 
 
-def _link(objs: list[str], out: str) -> None:
+def _link(objs: list[str], out: str, libs: tuple = ()) -> None:
     if not _newer(out, objs):
         return
-    cmd = [nvcc(), *ARCH, "-shared", "-o", out, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", out, *objs, *libs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed for {out}:\n{r.stderr}")
@@ -75,7 +75,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> dict:
         objs = [f.result() for f in futs]
         fsyn.result()
     lib = os.path.join(libdir, "librelax.so")
-    _link(sorted(objs), lib)
+    _link(sorted(objs), lib, ("-lcublas",))   # batched solves: X B and X' R products
     slib = os.path.join(synth_dir, "libsynth.so")
     _link([synth_obj], slib)
     if verbose:

@@ -1,5 +1,6 @@
 // C ABI of the library (include/relax.h): handle lifecycle, the solve loop,
 // FP64 certification and the standalone regularizer entry points.
+#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -203,6 +204,7 @@ inline unsigned grid_for(int64_t work, int block = 256) {
 
 // ================================================================== handle
 struct relax_handle {
+  cublasHandle_t cublas = nullptr;   // batched solves: X B and X' R products (created on first use)
   int dev = 0;
   cudaStream_t stream = nullptr;
   int64_t n = 0, p = 0;
@@ -213,6 +215,7 @@ struct relax_handle {
   relax_options opt{};
   double M = 2.0, eta = 0.0;
   int max_iters = 100000, chunk = 32;
+  int stall_min = 1000;      // least window of the stall rule (0: off)
   uint64_t limit_ns = 4000000000ull;
   bool certify = true;
   double L = 0.0;
@@ -267,6 +270,7 @@ void handle_free(relax_handle* h) {
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_d) cudaFreeHost(h->h_d);
   if (h->h_i) cudaFreeHost(h->h_i);
+  if (h->cublas) cublasDestroy(h->cublas);
   delete h;
 }
 
@@ -323,6 +327,7 @@ PArgs base_pargs(relax_handle* h) {
   a.rho = 2.0 * h->lambda2 / h->L;
   a.eta = h->eta;
   a.max_iters = h->max_iters;
+  a.stall_min = h->stall_min;
   a.lossp = nullptr;
   a.acc = h->acc;
   a.bpart = h->bpart;
@@ -654,6 +659,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     h->eta = o.eta == 0.0 ? std::exp(3.0) : o.eta;
     h->max_iters = o.max_iters == 0 ? 100000 : o.max_iters;
     h->chunk = o.chunk == 0 ? 32 : o.chunk;
+    h->stall_min = o.stall_window == 0 ? 1000 : std::max(0, o.stall_window);
     h->limit_ns = (uint64_t)(o.watchdog_ms == 0 ? 4000 : o.watchdog_ms) * 1000000ull;
     h->certify = o.no_certify == 0;
     const size_t es = h->esz();
@@ -804,6 +810,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.gap_ref = INFINITY;
   s.phi_best = INFINITY;
   s.psi_best = -INFINITY;
+  s.stall_gap = INFINITY;
   s.kbar = h->k - j1;
   s.pbar = jf;
   // With FP32 (or narrower) X the loop's gap is an estimate: aim a little below
@@ -951,7 +958,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     cert_dual = psi;
     const double crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
     if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel) || quantized ||
-        crel > 0.9 * prev_crel)
+        S0.stalled || crel > 0.9 * prev_crel)
       break;
     prev_crel = crel;
     ++cert_rounds;
@@ -984,6 +991,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     out->pphase_ms = pms_work;
   }
   out->restarts = S.restarts;
+  out->stalled = S.stalled;
   out->primal_loop = S.phi_best;
   out->dual_loop = S.psi_best;
   out->primal = have_cert ? cert_primal : S.phi_best;
@@ -1148,3 +1156,380 @@ relax_status gstar_persp(const void* alpha, int64_t p, int32_t k, double M, cons
 namespace relax {
 void set_error_detail(const char* msg) { snprintf(g_detail, sizeof(g_detail), "%s", msg); }
 }  // namespace relax
+
+// ======================================================= batched node solves
+// Many node relaxations of one design in lockstep: per iteration the active
+// nodes' points form the columns of B, Z = X B and G = X' R are two GEMMs
+// (FP32 data: FP32 emulated on the BF16 tensor cores; FP64: FP64), and the
+// p-phase of every active node runs in one segmented launch (waves when the
+// nodes' CTAs exceed what can be co-resident).  Converged nodes leave the
+// active set every kRetire iterations.
+namespace {
+
+constexpr int kRetire = 16;
+constexpr int kEmulateMin = 32;   // GEMM columns from which FP32 products use the tensor cores
+
+// B[:, s] = the next point of node active[s], in the storage type of X
+template <typename TX>
+__global__ void batch_pack_kernel(const IterState* st, const int* active, int m, int64_t p, TX* Bm) {
+  const int s = blockIdx.y;
+  if (s >= m) return;
+  const double* b = static_cast<const double*>(st[active[s]].ps.beta);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
+    Bm[(size_t)s * p + j] = (TX)b[j];
+}
+
+// z of node active[s] to its state, and the link: R[:, s] = grad F(z) and,
+// for the logistic loop, R[:, m + s] = grad F at the momentum point
+template <typename TX>
+__global__ void batch_link_kernel(const IterState* st, const int* active, int m, int64_t n, const TX* Z,
+                                  const double* y, int loss, TX* R) {
+  const int s = blockIdx.y;
+  if (s >= m) return;
+  const IterState& S = st[active[s]];
+  if (S.done) return;
+  double* zout = static_cast<double*>(S.ps.zout);
+  const double* zprev = static_cast<const double*>(S.ps.zprev);
+  const double mom = S.ps.mom;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double z = (double)Z[(size_t)s * n + i];
+    const double yd = y[i];
+    zout[i] = z;
+    if (loss == RELAX_LS) {
+      R[(size_t)s * n + i] = (TX)(2.0 * (z - yd));
+    } else {
+      R[(size_t)s * n + i] = (TX)(-yd / (1.0 + exp(yd * z)));
+      const double zy = (1.0 + mom) * z - mom * zprev[i];
+      R[(size_t)(m + s) * n + i] = (TX)(-yd / (1.0 + exp(yd * zy)));
+    }
+  }
+}
+
+// part[s][q][j] = G[j, q m + s] in FP64 (the p-phase's gradient layout)
+template <typename TX>
+__global__ void batch_grad_kernel(const TX* G, int m, int NB, int64_t p, double* part) {
+  const int s = blockIdx.y;
+  if (s >= m) return;
+  for (int q = 0; q < NB; ++q)
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
+      part[((size_t)s * NB + q) * p + j] = (double)G[(size_t)(q * m + s) * p + j];
+}
+
+__global__ void batch_done_kernel(const IterState* st, const int* active, int m, int* done) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x)
+    done[s] = st[active[s]].done;
+}
+
+relax_status cublas_status(cublasStatus_t c) {
+  if (c == CUBLAS_STATUS_SUCCESS) return RELAX_OK;
+  char msg[96];
+  snprintf(g_detail, sizeof(g_detail), "cuBLAS call failed: status %d", (int)c);
+  (void)msg;
+  return c == CUBLAS_STATUS_ALLOC_FAILED ? RELAX_ENOMEM : RELAX_ECUDA;
+}
+
+}  // namespace
+
+extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixings, const void* warm_start,
+                                          double gap_tol, void* beta_out, relax_result* out) {
+  if (!h || nb <= 0 || !beta_out || !out || !(gap_tol > 0.0)) return RELAX_EINVAL;
+  if (h->xk_loop != XK_F32 && h->xk_loop != XK_F64) return RELAX_ENOTSUP;   // BF16/FP8 storage: single solves
+  CU(cudaSetDevice(h->dev));
+  const int64_t n = h->n, p = h->p;
+  const bool f64 = h->xk_loop == XK_F64;
+  const size_t es = f64 ? 8 : 4;
+  const int NB = h->loss == RELAX_LS ? 1 : 2;
+  std::memset(out, 0, sizeof(relax_result) * (size_t)nb);
+  // ---- per-node fixing counts
+  std::vector<int> j1(nb, 0), jf(nb, (int)p);
+  if (fixings) {
+    int* cnt = nullptr;
+    relax_status rs0 = alloc((void**)&cnt, sizeof(int) * 3 * (size_t)nb);
+    if (rs0 != RELAX_OK) return rs0;
+    std::vector<int> hc(3 * (size_t)nb);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * (size_t)nb, h->stream);
+    for (int j = 0; j < nb && e == cudaSuccess; ++j) {
+      count_fix_kernel<<<grid_for(p), 256, 0, h->stream>>>(fixings + (size_t)j * p, p, cnt + 3 * j);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * 3 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(cnt);
+    if (e != cudaSuccess) { set_detail("fixing counts", e, __LINE__); return map_cuda(e); }
+    for (int j = 0; j < nb; ++j) {
+      if (hc[3 * j + 2] != 0 || hc[3 * j] > h->k) return RELAX_EINVAL;
+      j1[j] = hc[3 * j];
+      jf[j] = hc[3 * j + 1];
+    }
+  }
+  // ---- p-phase segments: one thread-block cluster per node when p fits one
+  // portable cluster (hardware barriers, one launch for every node), else the
+  // fewest CTAs that cover p in cooperative waves of co-resident segments
+  PPlan pp = h->pp_iter;
+  PPlan pc;
+  const bool clustered = pphase_cluster_plan(pc, p) == cudaSuccess && !std::getenv("RELAX_BATCH_WAVES");
+  cudaGetLastError();   // a refused cluster plan leaves no sticky error
+  const int segb = clustered ? pc.seg
+                             : (int)std::max<int64_t>(1, (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT));
+  const int wave = std::max(1, pp.maxgrid / segb);
+  if (!clustered && segb > pp.maxgrid) return RELAX_ENOTSUP;
+  // ---- device memory of the batch
+  const size_t nvec = 6 * (size_t)p + 3 * (size_t)n;   // per node: 6 p-vectors, 3 n-vectors (FP64)
+  IterState* dst = nullptr;
+  double* vec = nullptr;
+  unsigned long long* acc = nullptr;
+  double* bpart = nullptr;
+  unsigned long long* bars = nullptr;
+  void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;
+  double* part = nullptr;
+  int* active_d = nullptr;
+  int* done_d = nullptr;
+  relax_status rs = RELAX_OK;
+  auto cleanup = [&]() {
+    void* ptrs[] = {dst, vec, acc, bpart, bars, Bm, Zm, Rm, Gm, part, active_d, done_d};
+    for (void* q : ptrs) if (q) cudaFree(q);
+  };
+#define BTRY(x)                    \
+  do {                             \
+    rs = (x);                      \
+    if (rs != RELAX_OK) {          \
+      cudaStreamSynchronize(h->stream); \
+      cleanup();                   \
+      return rs;                   \
+    }                              \
+  } while (0)
+#define BTRYC(x)                                   \
+  do {                                             \
+    cudaError_t ec_ = (x);                         \
+    if (ec_ != cudaSuccess) {                      \
+      set_detail(#x, ec_, __LINE__);               \
+      cudaStreamSynchronize(h->stream);            \
+      cleanup();                                   \
+      return map_cuda(ec_);                        \
+    }                                              \
+  } while (0)
+  BTRY(alloc((void**)&dst, sizeof(IterState) * (size_t)nb));
+  BTRY(alloc((void**)&vec, sizeof(double) * nvec * (size_t)nb));
+  BTRY(alloc((void**)&acc, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)nb));
+  BTRY(alloc((void**)&bpart, sizeof(double) * 2 * (size_t)segb * NBP * (size_t)nb));
+  BTRY(alloc((void**)&bars, sizeof(unsigned long long) * (size_t)nb));
+  BTRY(alloc(&Bm, es * (size_t)p * nb));
+  BTRY(alloc(&Zm, es * (size_t)n * nb));
+  BTRY(alloc(&Rm, es * (size_t)n * NB * nb));
+  BTRY(alloc(&Gm, es * (size_t)p * NB * nb));
+  BTRY(alloc((void**)&part, sizeof(double) * (size_t)p * NB * nb));
+  BTRY(alloc((void**)&active_d, sizeof(int) * (size_t)nb));
+  BTRY(alloc((void**)&done_d, sizeof(int) * (size_t)nb));
+  BTRYC(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)nb, h->stream));
+  BTRYC(cudaMemsetAsync(bars, 0, sizeof(unsigned long long) * (size_t)nb, h->stream));
+  BTRYC(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  // ---- node states
+  std::vector<IterState> hs(nb);
+  const double loop_tol = f64 ? gap_tol : 0.7 * gap_tol;
+  for (int j = 0; j < nb; ++j) {
+    double* v = vec + nvec * (size_t)j;
+    IterState s{};
+    s.beta_prev = v;
+    s.beta_cur = v + p;
+    s.G_prev = v + 2 * p;
+    s.G_cur = v + 3 * p;
+    s.beta_best = v + 4 * p;
+    s.beta_dbest = v + 5 * p;
+    s.z_prev = v + 6 * p;
+    s.z_cur = v + 6 * p + n;
+    s.z_dbest = v + 6 * p + 2 * n;
+    s.tau = 1.0;
+    s.gap_ref = INFINITY;
+    s.phi_best = INFINITY;
+    s.psi_best = -INFINITY;
+    s.stall_gap = INFINITY;
+    s.kbar = h->k - j1[j];
+    s.pbar = jf[j];
+    s.tol = loop_tol;
+    s.ps.beta = s.beta_cur;
+    s.ps.zout = s.z_cur;
+    s.ps.zprev = s.z_prev;
+    s.ps.mom = 0.0;
+    hs[j] = s;
+    const void* w = warm_start ? static_cast<const unsigned char*>(warm_start) + es * (size_t)p * j : nullptr;
+    init_vectors_kernel<<<grid_for(std::max(p, n)), 256, 0, h->stream>>>(
+        w, f64 ? 1 : 0, (double*)s.beta_prev, (double*)s.beta_cur, (double*)s.beta_best, (double*)s.beta_dbest,
+        (double*)s.G_prev, (double*)s.G_cur, p, (double*)s.z_prev, (double*)s.z_cur, n);
+  }
+  BTRYC(cudaGetLastError());
+  BTRYC(cudaMemcpyAsync(dst, hs.data(), sizeof(IterState) * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
+  // ---- cuBLAS on the handle's stream
+  if (!h->cublas) {
+    cublasStatus_t c = cublasCreate(&h->cublas);
+    if (c != CUBLAS_STATUS_SUCCESS) { h->cublas = nullptr; BTRY(cublas_status(c)); }
+    cublasSetEmulationStrategy(h->cublas, CUBLAS_EMULATION_STRATEGY_EAGER);
+  }
+  BTRY(cublas_status(cublasSetStream(h->cublas, h->stream)));
+  // FP32 data: few columns make the products HBM-bound GEMVs, which plain FP32
+  // serves at the speed of reading X; from kEmulateMin columns on they are
+  // compute-bound and run as FP32 emulated on the BF16 tensor cores
+  const bool plain32 = std::getenv("RELAX_BATCH_FP32") != nullptr;   // FP32 on the FP32 pipes (comparison runs)
+  auto compute_type = [&](int cols) {
+    if (f64) return CUBLAS_COMPUTE_64F;
+    return (plain32 || cols < kEmulateMin) ? CUBLAS_COMPUTE_32F : CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  };
+  const cudaDataType_t dt = f64 ? CUDA_R_64F : CUDA_R_32F;
+  const double one64 = 1.0, zero64 = 0.0;
+  const float one32 = 1.0f, zero32 = 0.0f;
+  const void* one = f64 ? (const void*)&one64 : (const void*)&one32;
+  const void* zero = f64 ? (const void*)&zero64 : (const void*)&zero32;
+  // ---- p-phase arguments (segmented)
+  PArgs pa = base_pargs(h);
+  pa.mode = PM_ITER;
+  pa.fix = fixings;
+  pa.fix_stride = p;
+  pa.part = part;
+  pa.part_stride = (int64_t)NB * p;
+  pa.ncl = 1;
+  pa.NB = NB;
+  pa.st = dst;
+  pa.bar = bars;
+  pa.acc = acc;
+  pa.bpart = bpart;
+  pa.tol = loop_tol;
+  pa.fast_s1 = h->dtype == RELAX_F32 ? 1 : 0;
+  pa.lossp = nullptr;
+  pa.y = (const double*)h->y;
+  pa.n = n;
+  pa.seg_blocks = segb;
+  // ---- the loop
+  std::vector<int> active(nb), hdone(nb);
+  for (int j = 0; j < nb; ++j) active[j] = j;
+  const int max_rounds = h->max_iters / kRetire + 2;
+  int launches = 0;
+  for (int round = 0; round < max_rounds && !active.empty(); ++round) {
+    const int m = (int)active.size();
+    BTRYC(cudaMemcpyAsync(active_d, active.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, h->stream));
+    const dim3 gp((unsigned)std::min<int64_t>(64, (p + 255) / 256), (unsigned)m);
+    const dim3 gn((unsigned)std::min<int64_t>(64, (n + 255) / 256), (unsigned)m);
+    for (int it = 0; it < kRetire; ++it) {
+      if (f64) batch_pack_kernel<double><<<gp, 256, 0, h->stream>>>(dst, active_d, m, p, (double*)Bm);
+      else batch_pack_kernel<float><<<gp, 256, 0, h->stream>>>(dst, active_d, m, p, (float*)Bm);
+      // Z (n x m) = X (row-major n x ldx, i.e. column-major ldx x n) times B (p x m)
+      BTRY(cublas_status(cublasGemmEx(h->cublas, CUBLAS_OP_T, CUBLAS_OP_N, (int)n, m, (int)p, one, h->X, dt,
+                                      (int)h->ldx, Bm, dt, (int)p, zero, Zm, dt, (int)n, compute_type(m),
+                                      CUBLAS_GEMM_DEFAULT)));
+      if (f64) batch_link_kernel<double><<<gn, 256, 0, h->stream>>>(dst, active_d, m, n, (const double*)Zm, (const double*)h->y, h->loss, (double*)Rm);
+      else batch_link_kernel<float><<<gn, 256, 0, h->stream>>>(dst, active_d, m, n, (const float*)Zm, (const double*)h->y, h->loss, (float*)Rm);
+      // G (p x NB m) = X' R
+      BTRY(cublas_status(cublasGemmEx(h->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)p, NB * m, (int)n, one, h->X, dt,
+                                      (int)h->ldx, Rm, dt, (int)n, zero, Gm, dt, (int)p, compute_type(NB * m),
+                                      CUBLAS_GEMM_DEFAULT)));
+      if (f64) batch_grad_kernel<double><<<gp, 256, 0, h->stream>>>((const double*)Gm, m, NB, p, part);
+      else batch_grad_kernel<float><<<gp, 256, 0, h->stream>>>((const float*)Gm, m, NB, p, part);
+      BTRYC(cudaGetLastError());
+      if (clustered) {
+        PArgs pw = pa;
+        pw.seg_node = active_d;
+        pw.cluster = 1;
+        BTRYC(pphase_launch_clusters(pc, pw, m, h->stream));
+        ++launches;
+      } else {
+        for (int w0 = 0; w0 < m; w0 += wave) {
+          PArgs pw = pa;
+          pw.seg_node = active_d + w0;
+          pw.part = part + (size_t)w0 * NB * p;
+          const int cnt = std::min(wave, m - w0);
+          BTRYC(pphase_launch_grid(pp, pw, cnt * segb, h->stream));
+          ++launches;
+        }
+      }
+      launches += 5;
+    }
+    batch_done_kernel<<<1, 256, 0, h->stream>>>(dst, active_d, m, done_d);
+    BTRYC(cudaGetLastError());
+    BTRYC(cudaMemcpyAsync(hdone.data(), done_d, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+    BTRYC(cudaStreamSynchronize(h->stream));
+    int dstat = 0;
+    BTRYC(cudaMemcpy(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dstat != ST_OK) break;
+    std::vector<int> still;
+    for (int s = 0; s < m; ++s)
+      if (!hdone[s]) still.push_back(active[s]);
+    active.swap(still);
+  }
+  BTRYC(cudaMemcpyAsync(hs.data(), dst, sizeof(IterState) * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+  BTRYC(cudaStreamSynchronize(h->stream));
+  int dstat = 0;
+  BTRYC(cudaMemcpy(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  // ---- FP64 certificate of every node (two dual points, the better bound)
+  for (int j = 0; j < nb; ++j) {
+    const IterState& S = hs[j];
+    const int8_t* fx = fixings ? fixings + (size_t)j * p : nullptr;
+    relax_result& o = out[j];
+    o.lipschitz = h->L;
+    o.iters = S.iter;
+    o.restarts = S.restarts;
+    o.primal_loop = S.phi_best;
+    o.dual_loop = S.psi_best;
+    o.launches = launches;
+    relax_status st_j = map_dev_status(dstat);
+    if (h->certify && st_j == RELAX_OK) {
+      BTRY(certify(h, fx, S.beta_best, nullptr, S.z_dbest));
+      const double phi = h->h_d[0];
+      double psi = h->h_d[1];
+      BTRY(certify(h, fx, S.beta_best, S.beta_best, nullptr));
+      if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
+      o.primal = phi;
+      o.dual_bound = psi;
+    } else {
+      o.primal = S.phi_best;
+      o.dual_bound = S.psi_best;
+    }
+    o.gap = o.primal - o.dual_bound;
+    o.rel_gap = o.gap / std::max(1.0, std::fabs(o.primal));
+    from_f64_kernel<<<grid_for(p), 256, 0, h->stream>>>((const double*)S.beta_best,
+                                                         static_cast<unsigned char*>(beta_out) + es * (size_t)p * j,
+                                                         f64 ? 1 : 0, p);
+    o.stalled = S.stalled;
+    auto judge = [&](relax_status s0) {
+      if (s0 != RELAX_OK) return s0;
+      if (!std::isfinite(o.dual_bound) || std::isnan(o.primal)) return RELAX_ENUMERIC;
+      if (o.dual_bound > o.primal + 1e-9 * std::max(1.0, std::fabs(o.primal))) return RELAX_EINVALID_BOUND;
+      if (!(o.rel_gap <= gap_tol)) return RELAX_ENOTCONV;
+      return RELAX_OK;
+    };
+    st_j = judge(st_j);
+    if (st_j == RELAX_ENOTCONV && S.stalled && h->certify) {
+      // The node stalled on the floor of the batch's GEMM products (FP32
+      // accumulation over n or p terms): finish it with the single-node loop,
+      // whose fused pass forms the products with compensated sums, from the
+      // node's best point.  Both dual bounds are valid; the better one stays.
+      void* bj = static_cast<unsigned char*>(beta_out) + es * (size_t)p * j;
+      relax_result o2;
+      const relax_status r2 = relax_solve(h, fx, bj, gap_tol, bj, &o2);
+      if (r2 == RELAX_ECUDA || r2 == RELAX_ENOMEM || r2 == RELAX_ETIMEOUT || r2 == RELAX_EINVAL) {
+        cudaStreamSynchronize(h->stream);
+        cleanup();
+        return r2;
+      }
+      o.polish_iters = o2.iters;
+      o.launches += o2.launches;
+      if (r2 == RELAX_OK || r2 == RELAX_ENOTCONV) {
+        o.primal = o2.primal;            // Phi of the beta now in beta_out
+        o.dual_bound = std::max(o.dual_bound, o2.dual_bound);
+        o.stalled = o2.stalled;
+        o.gap = o.primal - o.dual_bound;
+        o.rel_gap = o.gap / std::max(1.0, std::fabs(o.primal));
+        st_j = judge(RELAX_OK);
+      } else {
+        st_j = r2;
+      }
+    }
+    o.status = st_j;
+  }
+  BTRYC(cudaGetLastError());
+  BTRYC(cudaStreamSynchronize(h->stream));
+  cleanup();
+#undef BTRY
+#undef BTRYC
+  relax_status worst = RELAX_OK;
+  for (int j = 0; j < nb; ++j)
+    if (out[j].status != RELAX_OK && worst == RELAX_OK) worst = (relax_status)out[j].status;
+  return worst;
+}

@@ -41,9 +41,19 @@ cudaError_t xstrip_launch(const XSPlan& pl, const XSArgs& a, cudaStream_t st);
 struct PPlan {
   const void* kernel = nullptr;
   int grid = 1;
+  int maxgrid = 1;         // CTAs that can be co-resident (cooperative launches)
   bool vdouble = false;
+  int seg = 0;             // cluster plans: CTAs per problem (the cluster size)
 };
 cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p);
 cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st);
+// the same kernel on `grid` CTAs (a segmented launch: grid = segments x a.seg_blocks <= maxgrid)
+cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaStream_t st);
+// Batched p-phase of many problems of length p, each on one thread-block
+// cluster of pl.seg CTAs with PEPT_CLUSTER coordinates per thread; fails with
+// cudaErrorNotSupported when p needs more CTAs than a portable cluster holds.
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p);
+// nseg clusters (a.seg_blocks = pl.seg, a.cluster = 1); no co-residency needed
+cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st);
 
 }  // namespace relax

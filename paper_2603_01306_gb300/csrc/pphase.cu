@@ -8,14 +8,15 @@ namespace relax {
 cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p) {
   pl = PPlan{};
   pl.vdouble = vdouble;
-  pl.kernel = vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double>)
-                      : reinterpret_cast<const void*>(&pphase_kernel<float>);
+  pl.kernel = vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>)
+                      : reinterpret_cast<const void*>(&pphase_kernel<float, PEPT>);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pl.kernel, PBLOCK, 0);
   if (e != cudaSuccess) return e;
   const int64_t maxgrid = (int64_t)nsm * std::max(per, 1);
+  pl.maxgrid = (int)maxgrid;
   // about two elements per thread; at most PEPT
   const int64_t want = (p + 2 * PBLOCK - 1) / (2 * PBLOCK);
   int64_t g = std::max<int64_t>(1, std::min<int64_t>(want, maxgrid));
@@ -26,11 +27,59 @@ cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p) {
 }
 
 cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st) {
+  return pphase_launch_grid(pl, a, pl.grid, st);
+}
+
+cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
-  cfg.gridDim = dim3(pl.grid, 1, 1);
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(PBLOCK, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[1] = {(void*)&a};
+  return cudaLaunchKernelExC(&cfg, pl.kernel, args);
+}
+
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p) {
+  pl = PPlan{};
+  pl.vdouble = true;
+  pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>);
+  const int64_t seg = (p + (int64_t)PBLOCK * PEPT_CLUSTER - 1) / ((int64_t)PBLOCK * PEPT_CLUSTER);
+  if (seg < 1 || seg > 8) return cudaErrorNotSupported;   // portable cluster size
+  pl.seg = (int)seg;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)seg;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)seg, 1, 1);
+  cfg.blockDim = dim3(PBLOCK, 1, 1);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, pl.kernel, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorNotSupported;
+  pl.maxgrid = nclusters * (int)seg;
+  pl.grid = (int)seg;
+  return cudaSuccess;
+}
+
+cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st) {
+  if (pl.seg < 1 || a.seg_blocks != pl.seg || !a.cluster || nseg < 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)pl.seg;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(nseg * pl.seg), 1, 1);
   cfg.blockDim = dim3(PBLOCK, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;

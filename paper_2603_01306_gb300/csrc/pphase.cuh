@@ -43,6 +43,7 @@ constexpr int PQ = 32;          // candidates per multisection round (one per la
 constexpr int PBLOCK = 256;
 constexpr int PNW = PBLOCK / 32;
 constexpr int PEPT = 4;         // max elements per thread
+constexpr int PEPT_CLUSTER = 8; // the same for the cluster-per-problem batched launch
 constexpr int NFIELD = 8;       // round accumulator fields
 constexpr int ACC_STRIDE = NFIELD * PQ;
 constexpr int NBP = 10;         // doubles per block partial
@@ -70,6 +71,9 @@ struct IterState {
   double phi_t, psi_t, g_t, c_last;
   double tol;                   // stop when (Phi_best - Psi_best) <= tol * max(1, |Phi_best|)
   int iter, restarts, have_ref, done, kbar, pbar, n_nz, n_top;
+  double stall_gap;             // best gap when it last fell by 10%
+  int stall_iter;               // iteration of that fall
+  int stalled;                  // 1: the loop stopped on the stall rule
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
 
@@ -80,6 +84,7 @@ struct PArgs {
   int k;                        // cardinality
   double lambda2, M, step, rho, eta, tol;
   int max_iters;
+  int stall_min;                // stall rule's least window (0: off)
   const int8_t* fix;            // NULL = root
   const void* part;             // [ncl][NB][p] doubles
   int ncl, NB;
@@ -98,6 +103,20 @@ struct PArgs {
   unsigned long long bar_base;  // used when st == NULL
   int* status;
   uint64_t limit_ns;
+  // Segmented launch (batched node solves, PM_ITER): seg_blocks > 0 splits
+  // the grid into segments of seg_blocks CTAs; segment s works on node
+  // seg_node[s] with its own state st[node], accumulators acc + node * 3 *
+  // ACC_STRIDE, block partials bpart + node * 2 * seg_blocks * NBP, barrier
+  // counter bar[node], fixings fix + node * fix_stride, and the gradients of
+  // its column, part + s * part_stride.  seg_blocks = 0: one problem, the
+  // whole grid.
+  int seg_blocks;
+  const int* seg_node;
+  int64_t fix_stride, part_stride;
+  // cluster = 1 (segmented launches only): every segment is one thread-block
+  // cluster of seg_blocks CTAs, whose hardware barrier replaces the counter
+  // barrier; segments are independent, so the grid needs no co-residency
+  int cluster;
 };
 
 template <typename T> __device__ __forceinline__ T huber_d(T a, T M) {
@@ -120,15 +139,38 @@ __device__ __forceinline__ unsigned long long fixp(double z) {
   return __double2ull_rz(z * 4294967296.0);
 }
 
+// The hardware barrier of a thread-block cluster, every thread of every CTA
+// of the cluster taking part; release / acquire at cluster scope orders the
+// CTAs' global-memory traffic around it, as the counter barrier does for a
+// cooperative grid.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // TV: element type of the p-vectors (double in the loop and certification;
-// float or double for the standalone entry points).
-template <typename TV>
-__global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
+// float or double for the standalone entry points).  EPT: elements per thread
+// (at most), so one CTA covers PBLOCK * EPT coordinates.
+template <typename TV, int EPT = PEPT>
+__global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   using KG = unsigned long long;   // S1 keys: FP32 or FP64 bit patterns of |a|
   using KV = uint32_t;             // FP32 keys of the S2 / S3 thresholds
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nthr = gridDim.x * PBLOCK;
-  const int gt = blockIdx.x * PBLOCK + tid;
+  // this CTA's problem: the whole grid, or its segment of a batched launch
+  const int nbk = a_in.seg_blocks > 0 ? a_in.seg_blocks : (int)gridDim.x;
+  const int seg = (int)blockIdx.x / nbk;
+  const int lbk = (int)blockIdx.x - seg * nbk;
+  PArgs a = a_in;
+  if (a_in.seg_blocks > 0) {
+    const int node = a_in.seg_node ? a_in.seg_node[seg] : seg;
+    a.st = a_in.st + node;
+    a.acc = a_in.acc + (size_t)node * 3 * ACC_STRIDE;
+    a.bpart = a_in.bpart + (size_t)node * 2 * nbk * NBP;
+    a.bar = a_in.bar + node;
+    if (a_in.fix) a.fix = a_in.fix + (size_t)node * a_in.fix_stride;
+    a.part = static_cast<const double*>(a_in.part) + (size_t)seg * a_in.part_stride;
+  }
+  const int nthr = nbk * PBLOCK;
+  const int gt = lbk * PBLOCK + tid;
   const int mode = a.mode;
   IterState* st = a.st;
 
@@ -147,13 +189,17 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   bool alive = true;
   auto barrier = [&]() {
     ++nbar;
-    if (alive && !grid_barrier(a.bar, bar0 + (unsigned long long)nbar * gridDim.x, a.limit_ns, a.status))
+    if (a_in.cluster) {
+      cluster_barrier();
+      return;
+    }
+    if (alive && !grid_barrier(a.bar, bar0 + (unsigned long long)nbar * nbk, a.limit_ns, a.status))
       alive = false;
   };
   int nstep = 0;
   // grid-wide deterministic FP64 sum of NV values
   auto gsum = [&](double* v, int nv) {
-    double* bp = a.bpart + (size_t)(nstep & 1) * gridDim.x * NBP;
+    double* bp = a.bpart + (size_t)(nstep & 1) * nbk * NBP;
     ++nstep;
     for (int i = 0; i < nv; ++i) {
       double s = warp_sum(v[i]);
@@ -163,12 +209,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     if (tid < nv) {
       double s = 0.0;
       for (int w = 0; w < PNW; ++w) s += red_d[w][tid];
-      bp[(size_t)blockIdx.x * NBP + tid] = s;
+      bp[(size_t)lbk * NBP + tid] = s;
     }
     barrier();
     for (int c = warp; c < nv; c += PNW) {
       double s = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(bp + (size_t)b * NBP + c);
+      for (int b = lane; b < nbk; b += 32) s += __ldcg(bp + (size_t)b * NBP + c);
       s = warp_sum(s);
       if (lane == 0) sh_tot[c] = s;
     }
@@ -189,7 +235,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       for (int w = 0; w < PNW; ++w) s += red_u[w][t];
       if (s) atomicAdd(accb + t, s);
     }
-    if (blockIdx.x == 0)
+    if (lbk == 0)
       for (int t = tid; t < ACC_STRIDE; t += PBLOCK) accz[t] = 0ull;
     barrier();
     for (int t = tid; t < nf * PQ; t += PBLOCK) sh_acc[t] = __ldcg(accb + t);
@@ -219,13 +265,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   // S1 keys: FP64 patterns when the values are FP64 and exactness is asked for
   const bool key64 = !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
 
-  int8_t fx[PEPT];
-  KG ka[PEPT];        // S1 keys: |a| on Jf, 0 elsewhere
-  TV bm[PEPT];        // S2: |beta| on Jf, 0 elsewhere
-  float bmf[PEPT];    // the same, rounded to FP32 for the multisection rounds
-  TV bt[PEPT];        // beta^t
-  double gg[PEPT];    // G^t
-  double gy[PEPT];    // logistic: X' grad F at the tentative y^t
+  int8_t fx[EPT];
+  KG ka[EPT];        // S1 keys: |a| on Jf, 0 elsewhere
+  TV bm[EPT];        // S2: |beta| on Jf, 0 elsewhere
+  float bmf[EPT];    // the same, rounded to FP32 for the multisection rounds
+  TV bt[EPT];        // beta^t
+  double gg[EPT];    // G^t
+  double gy[EPT];    // logistic: X' grad F at the tentative y^t
   // sums: 0 sum_J1 H(a), 1 sum_J1 b^2, 2 sum_Jf |b|, 3 sum_Jf b^2, 4 nnz_Jf(b),
   //       5 domain violations, 6 non-finite, 7 sum_Jf H(a), 8 F(z), 9 -F*(-zeta)
   double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -253,7 +299,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   const bool need_a = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GSTAR);
   const bool need_b = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GVAL);
 #pragma unroll
-  for (int e = 0; e < PEPT; ++e) {
+  for (int e = 0; e < EPT; ++e) {
     const int64_t j = (int64_t)gt + (int64_t)e * nthr;
     fx[e] = 0; ka[e] = 0; bm[e] = (TV)0; bmf[e] = 0.f; bt[e] = (TV)0; gg[e] = 0.0; gy[e] = 0.0;
     if (j >= p) { fx[e] = -2; continue; }
@@ -306,7 +352,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
   // standalone modes need |J1| and |Jf|; reuse the sum for counts
   double cnt2[2] = {0, 0};
   if (!st) {
-    for (int e = 0; e < PEPT; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       if (fx[e] > 0) cnt2[0] += 1.0;
       if (fx[e] == 0) cnt2[1] += 1.0;
     }
@@ -354,7 +400,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     const float inv2 = s2 ? 1.0f / w2 : 0.f;
     for (int src = 0; src < 32; ++src) {
 #pragma unroll
-      for (int e = 0; e < PEPT; ++e) {
+      for (int e = 0; e < EPT; ++e) {
         if (s1) {
           const KG kv = __shfl_sync(0xffffffffu, ka[e], src);
           fld[F_S1] += (kv >= x1) ? 1ull : 0ull;
@@ -413,7 +459,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (first && fin1) {
       const TV* av_src = mode == PM_GSTAR ? static_cast<const TV*>(a.vin) : nullptr;
-      for (int e = 0; e < PEPT; ++e) {
+      for (int e = 0; e < EPT; ++e) {
         if (fx[e] != 0) continue;
         const int64_t j = (int64_t)gt + (int64_t)e * nthr;
         const double aa = av_src ? fabs((double)av_src[j]) : fabs(gg[e]) / (2.0 * lam2);
@@ -422,7 +468,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       }
     }
     if (pol2) {
-      for (int e = 0; e < PEPT; ++e) {
+      for (int e = 0; e < EPT; ++e) {
         if ((double)bm[e] > wcur) {
           v[2] += 1.0;
           v[3] += (double)bm[e];
@@ -462,20 +508,21 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     psi = Dtot - 2.0 * lam2 * (tot[0] + topsum);
   }
   if (mode == PM_EVAL) {
-    if (blockIdx.x == 0 && tid == 0) {
+    if (lbk == 0 && tid == 0) {
       a.out[0] = phi;
       a.out[1] = psi;
       if (nonfinite) atomicCAS(a.status, ST_OK, ST_NUMERIC);
     }
   } else if (mode == PM_GVAL) {
-    if (blockIdx.x == 0 && tid == 0) a.out[0] = gval;
+    if (lbk == 0 && tid == 0) a.out[0] = gval;
   } else if (mode == PM_GSTAR) {
-    if (blockIdx.x == 0 && tid == 0) a.out[0] = tot[0] + topsum;
+    if (lbk == 0 && tid == 0) a.out[0] = tot[0] + topsum;
   }
 
   bool stop = false, restart = false, imp_p = false, imp_d = false;
   double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
-  int have_ref = 0, restarts = 0;
+  int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0;
+  double stall_gap = 0.0;
   const int t = st ? st->iter : 0;
   if (mode == PM_ITER) {
     const double tau = st->tau;
@@ -504,6 +551,21 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     }
     if (isfinite(phi_best) && phi_best - psi_best <= st->tol * fmax(1.0, fabs(phi_best))) stop = true;
     if (t >= a.max_iters) stop = true;
+    // Stall rule: with the gap restarts of Sec. 3.4 the best gap keeps falling
+    // (geometrically while the restarts fire, at least as 1/t^2 between them);
+    // one that has not fallen by 10% over the last quarter of the run, and over
+    // at least stall_min iterations, sits on the floor of the loop's
+    // arithmetic, and further iterations cannot lower it.
+    stall_gap = st->stall_gap;
+    stall_iter = st->stall_iter;
+    const double gbest = phi_best - psi_best;
+    if (!(gbest >= 0.9 * stall_gap)) {
+      stall_gap = gbest;
+      stall_iter = t;
+    } else if (a.stall_min > 0 && t - stall_iter >= max(a.stall_min, t / 4)) {
+      stop = true;
+      stalled = 1;
+    }
   }
 
   // best iterates (also on the stopping iteration); for the best dual value the
@@ -513,7 +575,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     TV* bbest = static_cast<TV*>(st->beta_best);
     TV* bdbest = static_cast<TV*>(st->beta_dbest);
 #pragma unroll
-    for (int e = 0; e < PEPT; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
       if (j >= p) continue;
       if (imp_p) bbest[j] = bt[e];
@@ -528,17 +590,17 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
 
   // ---------------------------------------------------------------- P1
   const bool do_prox = (mode == PM_PROX) || (mode == PM_ITER && !stop);
-  TV vv[PEPT];
-  TV mm[PEPT];      // |v| on Jf
-  float mmf[PEPT];  // |v| rounded to FP32 (rounds)
-  float ti[PEPT];   // T^{-1}(|v|) in FP32: where coordinate j reaches z_j = 1
+  TV vv[EPT];
+  TV mm[EPT];      // |v| on Jf
+  float mmf[EPT];  // |v| rounded to FP32 (rounds)
+  float ti[EPT];   // T^{-1}(|v|) in FP32: where coordinate j reaches z_j = 1
   double nzv = 0.0;
   if (do_prox) {
     const TV* vin = static_cast<const TV*>(a.vin);
     const TV muv = (TV)mu;
     const TV sv = (TV)a.step;
 #pragma unroll
-    for (int e = 0; e < PEPT; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
       vv[e] = (TV)0; mm[e] = (TV)0; mmf[e] = 0.f; ti[e] = 0.f;
       if (j >= p) continue;
@@ -587,7 +649,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       const float invw = (float)(1.0 / wq);
       for (int src = 0; src < 32; ++src) {
 #pragma unroll
-        for (int e = 0; e < PEPT; ++e) {
+        for (int e = 0; e < EPT; ++e) {
           const float m = __shfl_sync(0xffffffffu, mmf[e], src);
           const float tv = __shfl_sync(0xffffffffu, ti[e], src);
           if (m > cq) {
@@ -622,7 +684,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
       for (int it = 0; it <= MAX_POLISH; ++it) {
         const double Tc = (ccur <= rhoM) ? ccur * (1.0 + rho) / rho : ccur + M;
         double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int e = 0; e < PEPT; ++e) {
+        for (int e = 0; e < EPT; ++e) {
           if (fx[e] != 0) continue;
           const double m = (double)mm[e];
           if (m >= Tc) v[0] += 1.0;
@@ -653,7 +715,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
     double cnt[2] = {0, 0};
 #pragma unroll
-    for (int e = 0; e < PEPT; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
       if (j >= p) continue;
       const double v = (double)vv[e];
@@ -673,7 +735,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
     }
     if (mode == PM_PROX && a.counts) {
       gsum(cnt, 2);
-      if (blockIdx.x == 0 && tid == 0) {
+      if (lbk == 0 && tid == 0) {
         a.counts[0] = (int)cnt[0];
         a.counts[1] = (int)cnt[1];
       }
@@ -682,7 +744,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
 
   // ------------------------------------------------------------- epilogue
   barrier();   // everyone is done with the round accumulators
-  if (blockIdx.x == 0) {
+  if (lbk == 0) {
     for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
     if (tid == 0) {
       if (mode == PM_ITER) {
@@ -696,6 +758,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
         st->have_ref = have_ref;
         st->restarts = restarts;
         st->c_last = c;
+        st->stall_gap = stall_gap;
+        st->stall_iter = stall_iter;
+        st->stalled = stalled;
         if (stop) {
           st->done = 1;
           st->ps.done = 1;
@@ -719,7 +784,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a) {
           const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau_new * tau_new));
           st->ps.mom = (tau_new - 1.0) / tn;
         }
-        st->bar_base = bar0 + (unsigned long long)nbar * gridDim.x;
+        st->bar_base = bar0 + (unsigned long long)nbar * nbk;
       }
     }
   }

@@ -41,3 +41,25 @@ def test_strerror_is_host_only():
     assert relax.relax_strerror(0) == "ok"
     assert "invalid" in relax.relax_strerror(1)
     assert relax.relax_strerror(999) == "unknown status"
+
+
+def test_handle_rejects_mistyped_buffers():
+    """The C ABI takes bare pointers; the binding checks element type, length
+    and contiguity before handing a buffer over (an FP64 warm start given to
+    an FP32 handle would otherwise be read as FP32 words)."""
+    torch = pytest.importorskip("torch")
+    from paper_2603_01306_gb300.binding import Handle
+    h = object.__new__(Handle)
+    h.h, h.p, h.dtype = None, 5, torch.float32
+    h._vec(torch.zeros(5, dtype=torch.float32), "warm_start")
+    h._vec(torch.zeros((3, 5), dtype=torch.int8), "fixings", rows=3, dtype=torch.int8)
+    with pytest.raises(TypeError):
+        h._vec(torch.zeros(5, dtype=torch.float64), "warm_start")
+    with pytest.raises(TypeError):
+        h._vec(torch.zeros(5, dtype=torch.int32), "fixings", dtype=torch.int8)
+    with pytest.raises(ValueError):
+        h._vec(torch.zeros(6, dtype=torch.float32), "beta_out")
+    with pytest.raises(ValueError):
+        h._vec(torch.zeros((2, 5), dtype=torch.float32), "warm_start", rows=3)
+    with pytest.raises(ValueError):
+        h._vec(torch.zeros((5, 2), dtype=torch.float32)[:, 0], "beta")

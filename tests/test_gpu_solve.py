@@ -188,3 +188,21 @@ def test_solve_is_deterministic(lib):
     # the Lanczos estimate is within its 1% margin above ||X||^2 (times 2 for LS)
     lam = np.linalg.norm(X.astype(np.float64), 2) ** 2
     assert 2 * lam * 0.999 <= r0.lipschitz <= 2 * lam * 1.0101
+
+
+@pytest.mark.parametrize("loss", ["ls", "logistic"])
+def test_stall_rule_ends_a_solve_below_the_fp32_floor(lib, loss):
+    """A gap target that FP32 data cannot resolve (1e-13): the loop's best gap
+    stops falling, the stall rule ends the solve long before max_iters, the
+    status says the target was missed, and the certified bound stays valid and
+    as close to the optimum as the FP32 bar."""
+    w = synth.Workload("stall", 400, 900, 0.7, 10, 0.5, loss)
+    X, y = problem(w, dtype=np.float32)
+    X64, y64 = X.astype(np.float64), y.astype(np.float64)
+    L = solver.lipschitz(X64, loss)
+    opt = solver.solve(X64, y64, loss, w.k, w.lambda2, w.M, gap_tol=1e-12, L=L, max_iters=200000).dual_bound
+    beta, res, code = gpu_solve(lib, X, y, loss, w.k, w.lambda2, w.M, L, tol=1e-13, max_iters=100000)
+    assert code == 4, lib.STATUS[code]
+    assert res.iters < 20000, (res.iters, res.stalled)
+    assert res.dual_bound <= opt + 1e-12 * abs(opt)
+    assert res.dual_bound == pytest.approx(opt, rel=1e-6)
