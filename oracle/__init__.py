@@ -16,9 +16,11 @@ written from the paper's definitions and algorithms:
   Sec. 3.4; primal Phi (Eq. 6) and dual Psi (Eq. 7) with zeta = -grad F(X beta).
 * ``brute``: exact k-sparse optimum of problem (1) by support enumeration for
   tiny p, and the ridge closed form.
+* ``mlp``: the per-coordinate warm-start network (forward, MSE gradient by the
+  chain rule, Adam, BF16 rounding) and its input features.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` (worked examples, closed forms, Fenchel-Young
+``tests/test_oracle_pins.py`` and ``tests/test_oracle_mlp.py`` (worked examples, closed forms, Fenchel-Young
 equalities, brute force); none is "parity unpinned".
 """
-from . import regularizer, losses, solver, brute  # noqa: F401
+from . import regularizer, losses, solver, brute, mlp  # noqa: F401
