@@ -4,20 +4,25 @@ In branch and bound every child node is warm-started from its parent's
 solution (Sec. 5.3).  The learned variant keeps that start and adds a
 correction predicted coordinate by coordinate:
 
-    beta0_j = beta^P_j + f(x_j),
+    beta0_j = b_j + f(x_j),
 
 where x_j holds five features of coordinate j:
 
-    x_j = [ beta^P_j,                       the parent's solution
-            (X' grad F(X beta^P))_j,        the parent's gradient
+    x_j = [ b_j,                            the parent's solution on the child's set
+            (X' grad F(X b))_j,             the loss gradient there
             fix_j in {-1, 0, +1},           the child's fixing (J0, free, J1)
             ||X_j||_2,                      the column norm
             |corr(X_j, y)| ]                Pearson correlation with y
 
-and f is a multilayer perceptron 5 -> 64 -> 64 -> 1 with ReLU after both hidden
+with b = beta^P projected onto the child's fixings (zero on the child's J0):
+the gradient at b carries the effect of the branching on every other
+coordinate, which the gradient at beta^P itself (the same for both children)
+does not.
+
+f is a multilayer perceptron 5 -> 64 -> 64 -> 1 with ReLU after both hidden
 layers, whose inputs are standardised as (x - shift) / scale.  A network with
 zero output layer is exactly the parent warm start.  Training minimises the
-mean squared error between beta^P_j + f(x_j) and the child's converged beta_j.
+mean squared error between b_j + f(x_j) and the child's converged beta_j.
 
 Parameter vector (FP32 on the device, FP64 here), in this order:
     W1 (64 x 5, row h = hidden unit), b1 (64), W2 (64 x 64, row o = output
@@ -71,6 +76,14 @@ def init(seed=0, shift=None, scale=None):
     return theta
 
 
+def projected_parent(beta_parent, fix_child):
+    """b: the parent's solution with the child's J0 coordinates set to zero."""
+    b = np.array(beta_parent, dtype=np.float64)
+    if fix_child is not None:
+        b[np.asarray(fix_child) < 0] = 0.0
+    return b
+
+
 def parent_gradient(X, y, loss, beta):
     """X' grad F(X beta): the gradient of the loss term at the parent."""
     X = np.asarray(X, dtype=np.float64)
@@ -108,6 +121,14 @@ def forward(theta, F):
     h2 = np.maximum(a2, 0.0)
     out = h2 @ w3 + b3
     return out, (xs, a1, h1, a2, h2)
+
+
+def start(theta, F):
+    """The child's starting point: 0 on its J0 (feature 2 = -1), b + f(x)
+    elsewhere, with b = feature 0."""
+    F = np.asarray(F, dtype=np.float64)
+    out, _ = forward(theta, F)
+    return np.where(F[:, 2] < 0, 0.0, F[:, 0] + out)
 
 
 def loss_and_grad(theta, F, base, target):

@@ -15,8 +15,14 @@ RELAX_F64, RELAX_F32, RELAX_BF16, RELAX_FP8E4M3 = 0, 1, 2, 3
 STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA", 4: "RELAX_ENOTCONV",
           5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
 
-EXPORTS = ["relax_create", "relax_solve", "relax_xpass", "relax_certify", "relax_destroy",
-           "prox_persp", "gval_persp", "gstar_persp", "relax_strerror", "relax_error_detail"]
+EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_xpass", "relax_certify", "relax_destroy",
+           "prox_persp", "prox_persp_noalloc", "gval_persp", "gstar_persp",
+           "relax_mlp_features", "relax_mlp_forward", "relax_mlp_grad", "relax_mlp_adam",
+           "relax_strerror", "relax_error_detail"]
+
+# learned warm start (include/warmstart.h)
+MLP_NTRAIN = 4609
+MLP_NPARAM = 4619
 
 
 class RelaxError(RuntimeError):
@@ -74,6 +80,10 @@ def load():
     lib.prox_persp_noalloc.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
     lib.gval_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
     lib.gstar_persp.argtypes = [vp, i64, i32, dbl, vp, i32, ctypes.POINTER(dbl), vp]
+    lib.relax_mlp_features.argtypes = [vp, vp, vp, vp]
+    lib.relax_mlp_forward.argtypes = [vp, i32, vp, vp, i64, vp, vp]
+    lib.relax_mlp_grad.argtypes = [vp, i32, vp, vp, vp, i64, vp, vp, vp]
+    lib.relax_mlp_adam.argtypes = [vp, vp, vp, vp, i32, dbl, dbl, dbl, dbl, vp]
     lib.relax_strerror.argtypes = [ctypes.c_int]
     lib.relax_strerror.restype = ctypes.c_char_p
     lib.relax_error_detail.argtypes = []
@@ -184,6 +194,40 @@ def relax_certify(h, fixings, beta_primal, beta_dual):
     return float(out[0]), float(out[1])
 
 
+def relax_mlp_forward(theta, feat, out, base=None, bf16=True):
+    """out = base + f(feat) (f alone when base is None); float32 device tensors."""
+    _need_cuda(theta, feat, base, out)
+    _f32(theta, feat, base, out)
+    rows = feat.shape[0]
+    _check(load().relax_mlp_forward(_ptr(theta), 1 if bf16 else 0, _ptr(feat), _ptr(base), int(rows), _ptr(out),
+                                    _stream(feat.device)), "relax_mlp_forward")
+    return out
+
+
+def relax_mlp_grad(theta, feat, base, target, grad, loss=None, bf16=True):
+    """grad (and loss, a 1-element tensor) of mean (base + f(feat) - target)^2."""
+    _need_cuda(theta, feat, base, target, grad, loss)
+    _f32(theta, feat, base, target, grad, loss)
+    _check(load().relax_mlp_grad(_ptr(theta), 1 if bf16 else 0, _ptr(feat), _ptr(base), _ptr(target),
+                                 int(feat.shape[0]), _ptr(grad), _ptr(loss), _stream(feat.device)),
+           "relax_mlp_grad")
+    return grad
+
+
+def relax_mlp_adam(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _need_cuda(theta, grad, m, v)
+    _f32(theta, grad, m, v)
+    _check(load().relax_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr), float(beta1),
+                                 float(beta2), float(eps), _stream(theta.device)), "relax_mlp_adam")
+
+
+def _f32(*ts):
+    import torch
+    for t in ts:
+        if t is not None and (t.dtype != torch.float32 or not t.is_contiguous()):
+            raise TypeError("warm-start network buffers are contiguous float32 tensors")
+
+
 def relax_destroy(h):
     _check(load().relax_destroy(h), "relax_destroy")
 
@@ -288,6 +332,17 @@ class Handle:
         g = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
         loss = relax_xpass(self.h, beta, z, g)
         return z, g, loss
+
+    def mlp_features(self, beta_parent, fixings=None, out=None):
+        """(p, 5) float32 features of a child node (include/warmstart.h)."""
+        import torch
+        self._vec(beta_parent, "beta_parent")
+        self._vec(fixings, "fixings", dtype=torch.int8)
+        if out is None:
+            out = torch.empty((self.p, 5), dtype=torch.float32, device=self.X.device)
+        _f32(out)
+        _check(load().relax_mlp_features(self.h, _ptr(beta_parent), _ptr(fixings), _ptr(out)), "relax_mlp_features")
+        return out
 
     def certify(self, beta_primal, beta_dual=None, fixings=None):
         import torch

@@ -1,0 +1,169 @@
+"""Minimal best-first branch and bound over node relaxations (Sec. 5.3), the
+driver that produces (parent, child) node solves for the learned warm start
+and measures it against the parent warm start.
+
+* Node: fixings (int8 p: -1 J0, 0 free, +1 J1), its certified lower bound
+  (relax_solve's dual bound) and its solution beta.
+* Selection: the open node with the smallest bound.
+* Branching: the free coordinate with the largest |beta_j|; children fix it to
+  J0 and, while |J1| < k, to J1.
+* Incumbent: the support of the k largest |beta_j| (J1 first), solved as the
+  node that puts every other coordinate in J0; with no free coordinate the
+  relaxation is the restricted problem itself (Eq. 1 on that support), so its
+  value is a feasible objective.
+* Pruning: bound >= incumbent - rel_tol * max(1, |incumbent|).
+* Warm start of a child: the parent's beta ("parent"), or the learned start
+  b + f(x) of include/warmstart.h ("learned"), which falls back to the parent's
+  when its certified primal value is not lower.
+
+Every relaxation, pass and network evaluation runs in the CUDA library; this
+module keeps the queue.
+"""
+from __future__ import annotations
+
+import heapq
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(order=True)
+class Node:
+    bound: float
+    seq: int
+    fix: np.ndarray = field(compare=False)
+    beta: object = field(compare=False)       # device tensor (handle dtype)
+    iters: int = field(compare=False, default=0)
+
+
+@dataclass
+class BnBStats:
+    nodes: int = 0               # node relaxations solved (root and children)
+    iters: int = 0               # FISTA iterations of those solves
+    incumbent_solves: int = 0    # restricted solves of the incumbent heuristic (not in nodes / iters)
+    learned_used: int = 0        # children that started from the network
+    fallbacks: int = 0           # children where the parent start was kept
+    incumbent: float = float("inf")
+    best_bound: float = float("-inf")
+    certified: bool = False      # queue emptied: the incumbent is optimal
+    seconds: float = 0.0
+    pairs: list = field(default_factory=list)   # (parent beta, child fix, child beta) when recording
+
+
+def _branch_var(beta, fix):
+    score = np.where(fix == 0, np.abs(beta), -1.0)
+    j = int(np.argmax(score))
+    return j if score[j] > 0 else -1
+
+
+def _incumbent_fix(beta, fix, k):
+    order = np.argsort(-np.abs(beta), kind="stable")
+    sup = list(np.flatnonzero(fix > 0))
+    for j in order:
+        if len(sup) >= k:
+            break
+        if fix[j] == 0 and beta[j] != 0:
+            sup.append(int(j))
+    f = np.full(len(beta), -1, dtype=np.int8)
+    f[sup] = 1
+    return f
+
+
+def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False, rel_tol=1e-9):
+    """Best-first BnB on the handle's problem; stops when the queue empties
+    (certified) or after max_nodes relaxations."""
+    import torch
+    dev = h.X.device
+    st = BnBStats()
+    t0 = time.perf_counter()
+
+    def solve(fix, start, node=True):
+        fx = torch.tensor(fix, device=dev)
+        beta, res, code = h.solve(fixings=fx, warm_start=start, gap_tol=gap_tol)
+        if node:
+            st.nodes += 1
+            st.iters += res.iters
+        else:
+            st.incumbent_solves += 1
+        return beta, res, code
+
+    def learned(parent_beta, fix):
+        start, used = learned_start(h, net, parent_beta, torch.tensor(fix, device=dev))
+        if used:
+            st.learned_used += 1
+        else:
+            st.fallbacks += 1
+        return start
+
+    def try_incumbent(beta_np, fix):
+        f = _incumbent_fix(beta_np, fix, k)
+        _, res, code = solve(f, None, node=False)
+        if code in (0, 4) and res.primal < st.incumbent:
+            st.incumbent = res.primal
+
+    root = np.zeros(h.p, dtype=np.int8)
+    beta, res, code = solve(root, None)
+    heap = [Node(res.dual_bound, 0, root, beta, res.iters)]
+    try_incumbent(beta.double().cpu().numpy(), root)
+    seq = 1
+    while heap and st.nodes < max_nodes:
+        node = heapq.heappop(heap)
+        tol = rel_tol * max(1.0, abs(st.incumbent))
+        if node.bound >= st.incumbent - tol:
+            continue
+        b_np = node.beta.double().cpu().numpy()
+        j = _branch_var(b_np, node.fix)
+        if j < 0:
+            continue
+        kids = []
+        f0 = node.fix.copy()
+        f0[j] = -1
+        kids.append(f0)
+        if int(np.sum(node.fix > 0)) < k:
+            f1 = node.fix.copy()
+            f1[j] = 1
+            kids.append(f1)
+        for f in kids:
+            if st.nodes >= max_nodes:
+                break
+            start = learned(node.beta, f) if warm == "learned" else node.beta
+            beta, res, code = solve(f, start)
+            if record:
+                st.pairs.append((node.beta.clone(), f.copy(), beta.clone()))
+            if code not in (0, 4):
+                continue
+            if res.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
+                heapq.heappush(heap, Node(res.dual_bound, seq, f, beta, res.iters))
+                seq += 1
+                try_incumbent(beta.double().cpu().numpy(), f)
+    st.certified = not heap
+    st.best_bound = min([n.bound for n in heap], default=st.incumbent)
+    st.seconds = time.perf_counter() - t0
+    return st
+
+
+def learned_start(h, net, parent_beta, fixings):
+    """The learned start of a child (fixings: device int8), or the parent's
+    beta where the learned start has the higher certified Phi (FP64, +inf
+    outside dom g) than the parent's solution on the child's set.  Returns
+    (start, used_learned)."""
+    feat = h.mlp_features(parent_beta, fixings)
+    start = net.predict(feat).to(parent_beta.dtype)
+    phi_l, _ = h.certify(start, fixings=fixings)
+    phi_p, _ = h.certify(feat[:, 0].contiguous().to(parent_beta.dtype), fixings=fixings)
+    if not (phi_l > phi_p):
+        return start, True
+    return parent_beta, False
+
+
+def training_rows(h, pairs):
+    """Features, targets of every recorded (parent, child) pair, stacked:
+    (rows, 5) float32 and (rows,) float32 device tensors."""
+    import torch
+    feats, targets = [], []
+    for pb, fix, cb in pairs:
+        fx = torch.tensor(fix, device=h.X.device)
+        feats.append(h.mlp_features(pb, fx).clone())
+        targets.append(cb.float())
+    return torch.cat(feats), torch.cat(targets)

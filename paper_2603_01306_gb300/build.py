@@ -61,7 +61,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> dict:
     objdir = os.path.join(libdir, "obj")
     os.makedirs(objdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(csrc, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(csrc, "*.cuh"))) + [os.path.join(ROOT, "include", "relax.h")]
+    headers = sorted(glob.glob(os.path.join(csrc, "*.cuh"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
     incs = [csrc, os.path.join(ROOT, "include")]
     synth_src = os.path.join(ROOT, "synth", "gen.cu")
     synth_dir = os.path.join(ROOT, "synth", "_lib")

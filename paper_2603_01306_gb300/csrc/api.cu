@@ -14,6 +14,7 @@
 
 #include "launch.cuh"
 #include "relax.h"
+#include "warmstart.h"
 
 using namespace relax;
 
@@ -237,6 +238,7 @@ struct relax_handle {
   unsigned* xcnt = nullptr;      // per-pass zeroed area: block counters, max |beta|, fixed-point z
   double rowl1_x = 0.0;          // max_i ||x_i||_1 of X (NaN if X holds a NaN)
   double rowl1_q = 0.0;          // the same for the BF16/FP8 copy (stored values)
+  double* colstat = nullptr;     // [2][p]: ||X_j||_2, |corr(X_j, y)| (learned warm start)
   IterState* st = nullptr;
   PassState* ps_aux = nullptr;
   void* vb[13] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
@@ -263,7 +265,7 @@ void handle_free(relax_handle* h) {
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xg, h->lterm, h->xcnt, h->st,
-                  h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr};
+                  h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr, h->colstat};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (void* q : h->vb) if (q) cudaFree(q);
   if (h->h_state) cudaFreeHost(h->h_state);
@@ -1053,6 +1055,7 @@ relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g
     loss_host[0] = h->h_d[0];
     loss_host[1] = h->h_d[1];
   }
+  if (dst != ST_OK) snprintf(g_detail, sizeof(g_detail), "fused pass: device status %d", dst);
   return map_dev_status(dst);
 }
 
@@ -1532,4 +1535,103 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   for (int j = 0; j < nb; ++j)
     if (out[j].status != RELAX_OK && worst == RELAX_OK) worst = (relax_status)out[j].status;
   return worst;
+}
+
+// ================================================= learned warm start: features
+namespace {
+
+// per column j (one thread each; rows read in order, coalesced across j):
+// ||X_j||_2 and |corr(X_j, y)| from centred FP64 sums (two passes over X)
+template <typename T>
+__global__ void colstat_kernel(const T* X, int64_t n, int64_t p, int64_t ld, const double* y, double* out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
+  double sx = 0.0, sy = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    sx += (double)X[i * ld + j];
+    sy += y[i];
+  }
+  const double mx = sx / (double)n, my = sy / (double)n;
+  double sxx = 0.0, cxx = 0.0, cyy = 0.0, cxy = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = (double)X[i * ld + j];
+    const double dx = x - mx, dy = y[i] - my;
+    sxx += x * x;
+    cxx += dx * dx;
+    cyy += dy * dy;
+    cxy += dx * dy;
+  }
+  const double den = sqrt(cxx) * sqrt(cyy);
+  out[j] = sqrt(sxx);
+  out[p + j] = den > 0.0 ? fabs(cxy) / den : 0.0;
+}
+
+// b = beta^P with the child's J0 set to zero
+template <typename T>
+__global__ void project_parent_kernel(const T* beta, const int8_t* fix, int64_t p, T* b) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
+    b[j] = (fix && fix[j] < 0) ? (T)0 : beta[j];
+}
+
+template <typename T>
+__global__ void features_kernel(const T* beta, const T* g, const int8_t* fix, const double* colstat, int64_t p,
+                                float* feat) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x) {
+    float* f = feat + j * 5;
+    f[0] = (float)beta[j];
+    f[1] = (float)g[j];
+    f[2] = fix ? (float)fix[j] : 0.f;
+    f[3] = (float)colstat[j];
+    f[4] = (float)colstat[p + j];
+  }
+}
+
+}  // namespace
+
+extern "C" relax_status relax_mlp_features(relax_handle* h, const void* beta_parent, const int8_t* fixings,
+                                           float* feat_out) {
+  if (!h || !beta_parent || !feat_out) return RELAX_EINVAL;
+  CU(cudaSetDevice(h->dev));
+  const int64_t p = h->p;
+  if (!h->colstat) {
+    relax_status rs = alloc((void**)&h->colstat, sizeof(double) * 2 * (size_t)p);
+    if (rs != RELAX_OK) return rs;
+    const unsigned g = (unsigned)((p + 127) / 128);
+    if (h->dtype == RELAX_F64)
+      colstat_kernel<double><<<g, 128, 0, h->stream>>>((const double*)h->X, h->n, p, h->ldx, (const double*)h->y, h->colstat);
+    else
+      colstat_kernel<float><<<g, 128, 0, h->stream>>>((const float*)h->X, h->n, p, h->ldx, (const double*)h->y, h->colstat);
+    CU(cudaGetLastError());
+  }
+  // b (the parent on the child's set) and X' grad F(X b): one fused pass
+  void* gbuf = nullptr;
+  relax_status rs = alloc(&gbuf, 2 * h->esz() * (size_t)p);
+  if (rs != RELAX_OK) return rs;
+  void* bbuf = static_cast<unsigned char*>(gbuf) + h->esz() * (size_t)p;
+  if (h->dtype == RELAX_F64)
+    project_parent_kernel<double><<<grid_for(p), 256, 0, h->stream>>>((const double*)beta_parent, fixings, p, (double*)bbuf);
+  else
+    project_parent_kernel<float><<<grid_for(p), 256, 0, h->stream>>>((const float*)beta_parent, fixings, p, (float*)bbuf);
+  {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_detail("project_parent_kernel", e, __LINE__);
+      rs = map_cuda(e);
+    }
+  }
+  if (rs == RELAX_OK) rs = relax_xpass(h, bbuf, nullptr, gbuf, nullptr);
+  if (rs == RELAX_OK) {
+    if (h->dtype == RELAX_F64)
+      features_kernel<double><<<grid_for(p), 256, 0, h->stream>>>((const double*)bbuf, (const double*)gbuf,
+                                                                  fixings, h->colstat, p, feat_out);
+    else
+      features_kernel<float><<<grid_for(p), 256, 0, h->stream>>>((const float*)bbuf, (const float*)gbuf,
+                                                                 fixings, h->colstat, p, feat_out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { set_detail("features", e, __LINE__); rs = map_cuda(e); }
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(gbuf);
+  return rs;
 }
