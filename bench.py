@@ -39,7 +39,7 @@ WORKLOAD = "ls_20000x50000_f32"
 GAP_TOL = 1e-6
 # FISTA iterations the GPU solve of WORKLOAD needs to reach GAP_TOL (measured on
 # GB300 by this script's own arm; used by --impl reference to extrapolate).
-GPU_ITERS_TO_GAP = {"ls_20000x50000_f32": 929}
+GPU_ITERS_TO_GAP = {"ls_20000x50000_f32": 576}
 METRIC = "node relaxations/s to rel. gap 1e-6 on 1 GB300; fused X-pass HBM GB/s vs peak"
 PROFILE = os.path.join(ROOT, "profiles", "xstrip_ls_20000x50000_f32.md")
 
@@ -154,6 +154,13 @@ def run_ours(args):
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
+    if args.workload == BATCH_WORKLOAD:
+        # the batched-node workload alone (one JSON object, rank 0)
+        relax.load()
+        if rank != 0:
+            return None
+        return {"metric": "batched node relaxations/s to rel. gap 1e-6", **run_batch(device), "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded AR(1) Gaussian design)"}
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(device))
     relax.load()
@@ -268,7 +275,64 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(X_h, y_h, w, results[-1].lipschitz, statistics.median(iters),
                                             args.cpu_sample_iters)
+    if not args.no_batch:
+        del X_h, y_h
+        line["batch"] = run_batch(device)
     return line
+
+
+BATCH_WORKLOAD = "batch256_5000x10000_f32"
+
+
+def run_batch(device, workload=BATCH_WORKLOAD, reps=2, singles=16):
+    """Batched node relaxations: the nodes of one tree share X (5000 x 10000,
+    FP32); relax_solve_batch runs them in lockstep (X B and X' R GEMMs,
+    per-node p-phase, converged nodes retire).  Reported against the plain
+    FP32 single-node solve of the same nodes (the first `singles`)."""
+    import numpy as np
+    import torch
+    import paper_2603_01306_gb300 as relax
+    import synth
+    w = synth.WORKLOADS[workload]
+    nb = w.extra["nodes"]
+    X, y = synth.make_problem_gpu(w, device=device)
+    fix = np.stack([synth.node_fixings(w.p, 0, j, w.extra["j0_max"], w.extra["j1_max"], k=w.k) for j in range(nb)])
+    fixd = torch.tensor(fix, device=device)
+    h = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M)
+    stream = torch.cuda.current_stream()
+    times = []
+    for r in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, res, code = h.solve_batch(nb, fixings=fixd, gap_tol=GAP_TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        if code != 0:
+            raise RuntimeError(f"batch status {relax.STATUS[code]}")
+    t = min(times[1:]) if reps > 1 else times[0]
+    it = [r.iters for r in res]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    single_bounds = []
+    for j in range(singles):
+        _, r1, c1 = h.solve(fixings=fixd[j].contiguous(), gap_tol=GAP_TOL)
+        single_bounds.append(r1.dual_bound)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) * 1e-3
+    agree = max(abs(a - b.dual_bound) / abs(a) for a, b in zip(single_bounds, res))
+    h.close()
+    return {"workload": workload, "nodes": nb, "value": nb / t, "unit": "node relaxations/s",
+            "seconds": t, "iters_min_med_max": [min(it), int(np.median(it)), max(it)],
+            "polished_nodes": sum(1 for r in res if r.polish_iters > 0),
+            "max_certified_rel_gap": max(r.rel_gap for r in res),
+            "single_node_fp32": {"value": singles / ts, "unit": "node relaxations/s", "nodes": singles},
+            "max_rel_bound_diff_vs_single": agree,
+            "products": "cuBLAS GEMMs: FP32 emulated on the BF16 tensor cores from 32 active nodes, plain FP32 below"}
 
 
 def oracle_sample(Xh, yh, w, L, sample_iters):
@@ -352,13 +416,15 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="synthetic workload (ls_4000x50000_f32: the counter-capture case)")
+                    help="synthetic workload (ls_4000x50000_f32: the counter-capture case; "
+                         "batch256_5000x10000_f32: the batched-node measurement alone)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample-iters", type=int, default=12)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-iters", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-node measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         line = run_reference(args)

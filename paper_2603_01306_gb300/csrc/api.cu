@@ -1171,6 +1171,7 @@ namespace {
 
 constexpr int kRetire = 16;
 constexpr int kEmulateMin = 32;   // GEMM columns from which FP32 products use the tensor cores
+constexpr int kBatchStall = 200;  // least stall window inside a batch (iterations)
 
 // B[:, s] = the next point of node active[s], in the storage type of X
 template <typename TX>
@@ -1266,7 +1267,7 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     }
   }
   // ---- p-phase segments: one thread-block cluster per node when p fits one
-  // portable cluster (hardware barriers, one launch for every node), else the
+  // cluster (hardware barriers, one launch for every node), else the
   // fewest CTAs that cover p in cooperative waves of co-resident segments
   PPlan pp = h->pp_iter;
   PPlan pc;
@@ -1400,6 +1401,9 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   pa.y = (const double*)h->y;
   pa.n = n;
   pa.seg_blocks = segb;
+  // a node on the floor of the GEMM products hands over to the single-node
+  // finish after a shorter stall than a single solve waits
+  if (pa.stall_min > kBatchStall) pa.stall_min = kBatchStall;
   // ---- the loop
   std::vector<int> active(nb), hdone(nb);
   for (int j = 0; j < nb; ++j) active[j] = j;

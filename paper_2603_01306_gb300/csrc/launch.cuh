@@ -50,8 +50,9 @@ cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st);
 // the same kernel on `grid` CTAs (a segmented launch: grid = segments x a.seg_blocks <= maxgrid)
 cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaStream_t st);
 // Batched p-phase of many problems of length p, each on one thread-block
-// cluster of pl.seg CTAs with PEPT_CLUSTER coordinates per thread; fails with
-// cudaErrorNotSupported when p needs more CTAs than a portable cluster holds.
+// cluster of pl.seg CTAs: PEPT coordinates per thread on up to 16 CTAs where
+// the device allows that non-portable cluster size, else PEPT_CLUSTER on up to
+// 8; cudaErrorNotSupported when p needs more.
 cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p);
 // nseg clusters (a.seg_blocks = pl.seg, a.cluster = 1); no co-residency needed
 cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st);

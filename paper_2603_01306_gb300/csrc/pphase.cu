@@ -45,12 +45,22 @@ cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaSt
   return cudaLaunchKernelExC(&cfg, pl.kernel, args);
 }
 
-cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p) {
+// one cluster per problem: PEPT coordinates per thread (two CTAs fit an SM)
+// on up to 16 CTAs (a non-portable cluster size), else PEPT_CLUSTER per
+// thread on up to 8
+static cudaError_t cluster_try(PPlan& pl, int64_t p, const void* kernel, int ept, int max_seg) {
   pl = PPlan{};
   pl.vdouble = true;
-  pl.kernel = reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>);
-  const int64_t seg = (p + (int64_t)PBLOCK * PEPT_CLUSTER - 1) / ((int64_t)PBLOCK * PEPT_CLUSTER);
-  if (seg < 1 || seg > 8) return cudaErrorNotSupported;   // portable cluster size
+  pl.kernel = kernel;
+  const int64_t seg = (p + (int64_t)PBLOCK * ept - 1) / ((int64_t)PBLOCK * ept);
+  if (seg < 1 || seg > max_seg) return cudaErrorNotSupported;
+  if (seg > 8) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+  }
   pl.seg = (int)seg;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -64,11 +74,20 @@ cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p) {
   cfg.numAttrs = 1;
   int nclusters = 0;
   cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, pl.kernel, &cfg);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
   if (nclusters < 1) return cudaErrorNotSupported;
   pl.maxgrid = nclusters * (int)seg;
   pl.grid = (int)seg;
   return cudaSuccess;
+}
+
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p) {
+  if (cluster_try(pl, p, reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>), PEPT, 16) == cudaSuccess)
+    return cudaSuccess;
+  return cluster_try(pl, p, reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>), PEPT_CLUSTER, 8);
 }
 
 cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st) {
