@@ -71,6 +71,7 @@ struct IterState {
   double phi_t, psi_t, g_t, c_last;
   double tol;                   // stop when (Phi_best - Psi_best) <= tol * max(1, |Phi_best|)
   int iter, restarts, have_ref, done, kbar, pbar, n_nz, n_top;
+  double t1_last, w2_last;      // S1's t* and S2's water level of the last iteration (0: none)
   double stall_gap;             // best gap when it last fell by 10%
   int stall_iter;               // iteration of that fall
   int stalled;                  // 1: the loop stopped on the stall rule
@@ -130,6 +131,22 @@ __device__ __forceinline__ KT cand(KT lo, KT hi, int q) {
   const KT d = hi - lo - 1;
   const KT qq = (KT)(q + 1);
   return lo + 1 + (d / (KT)(PQ + 1)) * qq + ((d % (KT)(PQ + 1)) * qq) / (KT)(PQ + 1);
+}
+
+// First-round candidates around the previous iteration's threshold key kc:
+// lane q sits at kc - 2^(15-q) (q < 16), kc (q = 16), kc + 2^(q-17) (q > 16),
+// offsets in units of 2^shift keys, clamped into (lo, hi).  The thresholds move
+// little from one iteration to the next, so after this round the bracket is
+// about as wide as the move; the rounds that follow split it uniformly.  Any
+// candidates inside (lo, hi) keep the bracket's invariant, so the result is
+// the same as from uniform rounds.
+template <typename KT>
+__device__ __forceinline__ KT warm_cand(KT kc, KT lo, KT hi, int q, int shift) {
+  long long off = q < 16 ? -(1ll << (15 - q)) : (q == 16 ? 0ll : (1ll << (q - 17)));
+  long long x = (long long)kc + off * (1ll << shift);
+  if (x <= (long long)lo) x = (long long)lo + 1;
+  if (x >= (long long)hi) x = (long long)hi - 1;
+  return (KT)x;
 }
 
 __device__ __forceinline__ unsigned long long fixp(float z) {
@@ -392,10 +409,20 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
 
   // ------------------------------------------------------- S1 / S2 rounds
+  // warm first rounds from the last iteration's t* and water level (loop only)
+  const double t1p = (mode == PM_ITER) ? st->t1_last : 0.0;
+  const double w2p = (mode == PM_ITER) ? st->w2_last : 0.0;
+  bool warm1 = s1 && t1p > 0.0 && isfinite(t1p);
+  bool warm2 = s2 && w2p > 0.0 && isfinite(w2p);
+  const KG kc1 = warm1 ? (key64 ? (KG)key_of(t1p) : (KG)key_of((float)t1p)) : (KG)0;
+  const KV kc2 = warm2 ? key_of((float)w2p) : (KV)0;
+  const int sh1 = key64 ? 29 : 0;   // FP64 keys: 29 more mantissa bits per FP32 step
+  auto cand1 = [&](int q) { return warm1 ? warm_cand<KG>(kc1, lo1, hi1, q, sh1) : cand<KG>(lo1, hi1, q); };
+  auto cand2 = [&](int q) { return warm2 ? warm_cand<KV>(kc2, lo2, hi2, q, 0) : cand<KV>(lo2, hi2, q); };
   while (s1 || s2) {
     unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const KG x1 = s1 ? cand<KG>(lo1, hi1, lane) : (KG)0;
-    const KV x2 = s2 ? cand<KV>(lo2, hi2, lane) : (KV)0;
+    const KG x1 = s1 ? cand1(lane) : (KG)0;
+    const KV x2 = s2 ? cand2(lane) : (KV)0;
     const float w2 = from_key(x2, 0.f);
     const float inv2 = s2 ? 1.0f / w2 : 0.f;
     for (int src = 0; src < 32; ++src) {
@@ -420,11 +447,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       // largest candidate with count >= kb -> new lo; smallest with count < kb -> new hi
       KG nlo = lo1, nhi = hi1;
       for (int q = 0; q < PQ; ++q) {
-        const KG xq = cand<KG>(lo1, hi1, q);
+        const KG xq = cand1(q);
         if (sh_acc[F_S1 * PQ + q] >= (unsigned long long)kb) { if (xq > nlo) nlo = xq; }
         else if (xq < nhi) nhi = xq;
       }
       lo1 = nlo; hi1 = nhi;
+      warm1 = false;
       if (hi1 - lo1 <= 1) s1 = false;
     }
     if (s2) {
@@ -432,12 +460,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       double nclo = c2lo, nchi = c2hi;
       const unsigned long long thr = (unsigned long long)kb << 32;
       for (int q = 0; q < PQ; ++q) {
-        const KV xq = cand<KV>(lo2, hi2, q);
+        const KV xq = cand2(q);
         const double cq = (double)sh_acc[F_S2C * PQ + q];
         if (sh_acc[F_S2Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nclo = cq; } }
         else if (xq < nhi) { nhi = xq; nchi = cq; }
       }
       lo2 = nlo; hi2 = nhi; c2lo = nclo; c2hi = nchi;
+      warm2 = false;
       if (c2lo == c2hi || hi2 - lo2 <= 1) s2 = false;
     }
   }
@@ -454,6 +483,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   double nprev = -1.0;
   const double wlo = (double)from_key(lo2, 0.f), whi = (double)from_key(hi2, 0.f);
   int npol = 0;
+  double wlast = 0.0;   // the water level found (0: none)
   bool first = true;
   while (first || pol2) {
     double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -491,6 +521,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         const bool stable = (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
         if (stable || npol >= MAX_POLISH) {
           gval = 0.5 * (tot[1] + Qab + wn * Sbel);
+          wlast = wn;
           pol2 = false;
         } else {
           nprev = Nab;
@@ -640,9 +671,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     else if (nzv <= (double)kb) c = 0.0;
     else s3 = true;
     const double rhoM = rho * M;
+    const double c3p = (mode == PM_ITER) ? st->c_last : 0.0;
+    bool warm3 = s3 && c3p > 0.0 && isfinite(c3p);
+    const KV kc3 = warm3 ? key_of((float)c3p) : (KV)0;
+    auto cand3 = [&](int q) { return warm3 ? warm_cand<KV>(kc3, lo3, hi3, q, 0) : cand<KV>(lo3, hi3, q); };
     while (s3) {
       unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
-      const KV x3 = cand<KV>(lo3, hi3, lane);
+      const KV x3 = cand3(lane);
       const float cq = from_key(x3, 0.f);
       const double cqd = (double)cq;
       const double wq = fmin(cqd / rho, M);
@@ -666,12 +701,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       double nmlo = cmlo, nmhi = cmhi, ntlo = ctlo, nthi = cthi;
       const unsigned long long thr = (unsigned long long)kb << 32;
       for (int q = 0; q < PQ; ++q) {
-        const KV xq = cand<KV>(lo3, hi3, q);
+        const KV xq = cand3(q);
         const double cm = (double)sh_acc[F_S3CM * PQ + q], ct = (double)sh_acc[F_S3CT * PQ + q];
         if (sh_acc[F_S3Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nmlo = cm; ntlo = ct; } }
         else if (xq < nhi) { nhi = xq; nmhi = cm; nthi = ct; }
       }
       lo3 = nlo; hi3 = nhi; cmlo = nmlo; cmhi = nmhi; ctlo = ntlo; cthi = nthi;
+      warm3 = false;
       const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
       const bool regime_inside = (rhoM > clo && rhoM <= chi);
       if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
@@ -758,6 +794,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         st->have_ref = have_ref;
         st->restarts = restarts;
         st->c_last = c;
+        st->t1_last = fin1 ? tstar : 0.0;
+        st->w2_last = wlast;
         st->stall_gap = stall_gap;
         st->stall_iter = stall_iter;
         st->stalled = stalled;
