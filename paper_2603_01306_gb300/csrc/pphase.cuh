@@ -396,6 +396,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     else if (pb <= kb) topsum = tot[7];
     else s1 = true;
   }
+  // In the loop beta^t (t >= 1) is the prox output of the last iteration, whose
+  // threshold c fixes its water level: stationarity of the prox in beta_j and
+  // the water filling in z_j give |beta_j| = |v_j| - rho w on the fractional
+  // coordinates, i.e. w = c / rho (M at most), the w of the prox's own
+  // z_j(c).  g then needs one classification at w instead of S2's rounds.
+  const double c_prev = (mode == PM_ITER) ? st->c_last : 0.0;
+  const bool w_known = mode == PM_ITER && st->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
+  const double w_closed = w_known ? fmin(c_prev / rho, M) : 0.0;
   bool g_inf = false;
   if (need_b) {
     const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (g_inf) gval = INFINITY;
     else if (kb <= 0) gval = 0.5 * tot[1];
     else if (tot[4] <= (double)kb) gval = 0.5 * (tot[1] + tot[3]);
-    else { s2 = true; c2lo = tot[4]; c2hi = 0.0; }
+    else if (!w_known) { s2 = true; c2lo = tot[4]; c2hi = 0.0; }
   }
 
   // ------------------------------------------------------- S1 / S2 rounds
@@ -479,7 +487,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
                                      : (double)from_key((uint32_t)lo1, 0.f)) : 0.0;
   const double htstar = huber_d<double>(tstar, M);
   bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb;
-  double wcur = pol2 ? (double)from_key(hi2, 0.f) : 0.0;
+  double wcur = pol2 ? (w_known ? w_closed : (double)from_key(hi2, 0.f)) : 0.0;
   double nprev = -1.0;
   const double wlo = (double)from_key(lo2, 0.f), whi = (double)from_key(hi2, 0.f);
   int npol = 0;
@@ -518,7 +526,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         pol2 = false;
       } else {
         const double wn = Sbel / ((double)kb - Nab);
-        const bool stable = (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
+        // the closed-form level classifies exactly: one pass (a coordinate with
+        // |beta_j| = w adds w |beta_j| = beta_j^2 on either side)
+        const bool stable = w_known || (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
         if (stable || npol >= MAX_POLISH) {
           gval = 0.5 * (tot[1] + Qab + wn * Sbel);
           wlast = wn;
