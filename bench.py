@@ -44,6 +44,22 @@ METRIC = "node relaxations/s to rel. gap 1e-6 on 1 GB300; fused X-pass HBM GB/s 
 PROFILE = os.path.join(ROOT, "profiles", "xstrip_ls_20000x50000_f32.md")
 
 
+def max_over_ranks(ms, world, device="cpu"):
+    """The slowest rank's time: every rank returns the maximum (one all-reduce;
+    the only collective of a run, outside the timed region)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank, world, ms_max):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -192,10 +208,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
     ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, device)
     clocks = clk.summary()
     # ---- end to end through the public API, from pinned host buffers
     X_h = torch.empty(tuple(X.shape), dtype=torch.float32).pin_memory()
@@ -235,7 +248,7 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic = profile_traffic()
-    value = world * args.steps / (ms_max * 1e-3)
+    value = throughput(args.steps, world, ms_max)
     line = {
         "metric": METRIC,
         "value": value,

@@ -1226,9 +1226,7 @@ __global__ void batch_done_kernel(const IterState* st, const int* active, int m,
 
 relax_status cublas_status(cublasStatus_t c) {
   if (c == CUBLAS_STATUS_SUCCESS) return RELAX_OK;
-  char msg[96];
   snprintf(g_detail, sizeof(g_detail), "cuBLAS call failed: status %d", (int)c);
-  (void)msg;
   return c == CUBLAS_STATUS_ALLOC_FAILED ? RELAX_ENOMEM : RELAX_ECUDA;
 }
 

@@ -297,16 +297,13 @@ relax_status relax_mlp_grad(const float* theta, int32_t bf16, const float* feat,
                             const float* target, int64_t rows, float* grad, float* loss, void* stream) {
   if (!theta || !feat || !base || !target || !grad || rows <= 0) return RELAX_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
-    if (e != cudaSuccess) return cuda_status(e);
-    attr_set = true;
-  }
+  // per device (the current one): cheap, so set on every call
+  cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+  if (e != cudaSuccess) return cuda_status(e);
   const int64_t ntiles = (rows + TILE - 1) / TILE;
   const int nparts = (int)(ntiles < sm_count() ? ntiles : sm_count());
   float* part = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&part, (size_t)nparts * (RELAX_MLP_NTRAIN + 1) * sizeof(float), st);
+  e = cudaMallocAsync((void**)&part, (size_t)nparts * (RELAX_MLP_NTRAIN + 1) * sizeof(float), st);
   if (e != cudaSuccess) return cuda_status(e);
   mlp_grad_kernel<<<nparts, TILE, grad_smem(), st>>>(theta, bf16 ? 1 : 0, feat, base, target, rows, part);
   e = cudaGetLastError();
