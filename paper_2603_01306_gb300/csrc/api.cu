@@ -560,17 +560,18 @@ relax_status count_fixings(relax_handle* h, const int8_t* fix, int* j1, int* jf)
 // FP64 Phi(beta_p) and Psi(zeta) with the master X -> h->h_d[0..1].
 // zeta = -grad F(X beta_d) when zd == NULL, else zeta = -grad F(zd) (a dual
 // point given by its z).
-relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd, const void* zd) {
-  const XSPlan& pl = zd ? h->pl_certz : h->pl_cert;
-  PassState ps{};
-  ps.beta = bp;
-  ps.beta2 = zd ? nullptr : bd;
-  ps.zprev = zd;
-  *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
-  CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-  const int link = zd ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
-                      : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
-  XSArgs a = pass_args(h, pl, link, h->ps_aux);
+// Enqueue the FP64 certificate of one point pair on the handle's stream:
+// {Phi(bp), Psi(zeta)} into out_dev[0..1], zeta = -grad F(z_d) when the pass
+// state names z_d (zprev), else -grad F(X bd).  ps_dev: the pass state in
+// device memory (beta = bp, beta2 = bd or NULL, zprev = z_d or NULL).  No
+// host synchronisation; consecutive calls share the handle's scratch in
+// stream order.
+relax_status certify_enqueue(relax_handle* h, const int8_t* fix, const void* bp, bool dual_from_z,
+                             PassState* ps_dev, double* out_dev) {
+  const XSPlan& pl = dual_from_z ? h->pl_certz : h->pl_cert;
+  const int link = dual_from_z ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
+                               : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
+  XSArgs a = pass_args(h, pl, link, ps_dev);
   a.colscale = nullptr;
   a.lterm = h->lterm;
   CU(run_pass(h, pl, a, h->stream));
@@ -582,7 +583,7 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
   pa.NB = 1;
   pa.st = nullptr;
   pa.vin = bp;
-  pa.out = h->dscr;
+  pa.out = out_dev;
   pa.fast_s1 = 0;
   pa.lossp = h->lterm;
   pa.n = h->n;
@@ -590,6 +591,18 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
   pa.bar_base = 0;
   CU(cudaMemsetAsync(h->bar_aux, 0, sizeof(unsigned long long), h->stream));
   CU(pphase_launch(h->pp_eval, pa, h->stream));
+  return RELAX_OK;
+}
+
+relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd, const void* zd) {
+  PassState ps{};
+  ps.beta = bp;
+  ps.beta2 = zd ? nullptr : bd;
+  ps.zprev = zd;
+  *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
+  CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
+  relax_status rs = certify_enqueue(h, fix, bp, zd != nullptr, h->ps_aux, h->dscr);
+  if (rs != RELAX_OK) return rs;
   CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   return RELAX_OK;
@@ -1462,7 +1475,47 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   BTRYC(cudaStreamSynchronize(h->stream));
   int dstat = 0;
   BTRYC(cudaMemcpy(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost));
-  // ---- FP64 certificate of every node (two dual points, the better bound)
+  // ---- FP64 certificate of every node (two dual points, the better bound):
+  // all passes enqueued back to back, one synchronisation
+  std::vector<double> cert(4 * (size_t)nb, 0.0);
+  if (h->certify && map_dev_status(dstat) == RELAX_OK) {
+    PassState* psd = nullptr;
+    double* certd = nullptr;
+    BTRY(alloc((void**)&psd, sizeof(PassState) * 2 * (size_t)nb));
+    relax_status rsa = alloc((void**)&certd, sizeof(double) * 4 * (size_t)nb);
+    if (rsa != RELAX_OK) { cudaFree(psd); BTRY(rsa); }
+    std::vector<PassState> pss(2 * (size_t)nb);
+    for (int j = 0; j < nb; ++j) {
+      PassState a{}, b{};
+      a.beta = hs[j].beta_best;            // Phi(beta_best), Psi at the loop's dual point
+      a.zprev = hs[j].z_dbest;
+      b.beta = hs[j].beta_best;            // Psi at zeta = -grad F(X beta_best)
+      b.beta2 = hs[j].beta_best;
+      pss[2 * j] = a;
+      pss[2 * j + 1] = b;
+    }
+    auto chk = [&](cudaError_t e, const char* what, int line) {
+      if (e == cudaSuccess) return RELAX_OK;
+      set_detail(what, e, line);
+      return map_cuda(e);
+    };
+    relax_status rc = chk(cudaMemcpyAsync(psd, pss.data(), sizeof(PassState) * 2 * (size_t)nb,
+                                          cudaMemcpyHostToDevice, h->stream), "pass states to device", __LINE__);
+    for (int j = 0; j < nb && rc == RELAX_OK; ++j) {
+      const int8_t* fx = fixings ? fixings + (size_t)j * p : nullptr;
+      rc = certify_enqueue(h, fx, hs[j].beta_best, true, psd + 2 * j, certd + 4 * j);
+      if (rc == RELAX_OK) rc = certify_enqueue(h, fx, hs[j].beta_best, false, psd + 2 * j + 1, certd + 4 * j + 2);
+    }
+    if (rc == RELAX_OK)
+      rc = chk(cudaMemcpyAsync(cert.data(), certd, sizeof(double) * 4 * (size_t)nb, cudaMemcpyDeviceToHost,
+                               h->stream), "certificates to host", __LINE__);
+    if (rc == RELAX_OK) rc = chk(cudaStreamSynchronize(h->stream), "certificate passes", __LINE__);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(psd);
+    cudaFree(certd);
+    BTRY(rc);
+    // a non-finite certificate shows in that node's own values (judged below)
+  }
   for (int j = 0; j < nb; ++j) {
     const IterState& S = hs[j];
     const int8_t* fx = fixings ? fixings + (size_t)j * p : nullptr;
@@ -1472,14 +1525,13 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     o.restarts = S.restarts;
     o.primal_loop = S.phi_best;
     o.dual_loop = S.psi_best;
-    o.launches = launches;
+    o.launches = launches + (h->certify ? 4 * nb : 0);
     relax_status st_j = map_dev_status(dstat);
     if (h->certify && st_j == RELAX_OK) {
-      BTRY(certify(h, fx, S.beta_best, nullptr, S.z_dbest));
-      const double phi = h->h_d[0];
-      double psi = h->h_d[1];
-      BTRY(certify(h, fx, S.beta_best, S.beta_best, nullptr));
-      if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
+      const double phi = cert[4 * (size_t)j];
+      double psi = cert[4 * (size_t)j + 1];
+      const double psi2 = cert[4 * (size_t)j + 3];
+      if (psi2 > psi || !(psi == psi)) psi = psi2;
       o.primal = phi;
       o.dual_bound = psi;
     } else {
