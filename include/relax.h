@@ -59,7 +59,7 @@ typedef enum {
   RELAX_ETIMEOUT = 5,        /* a bounded device-side wait expired */
   RELAX_ENUMERIC = 6,        /* NaN/Inf met in the data or the iterates */
   RELAX_EINVALID_BOUND = 7,  /* certified dual bound above certified primal beyond rounding */
-  RELAX_ENOTSUP = 8          /* shape or option outside what this build supports */
+  RELAX_ENOTSUP = 8          /* shape or option outside what this library supports */
 } relax_status;
 
 /* Solver options.  A zero-initialised struct means "all defaults". */

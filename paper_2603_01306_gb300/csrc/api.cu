@@ -624,7 +624,7 @@ const char* relax_strerror(relax_status s) {
     case RELAX_ETIMEOUT: return "a bounded device-side wait expired";
     case RELAX_ENUMERIC: return "non-finite value in the data or the iterates";
     case RELAX_EINVALID_BOUND: return "certified dual bound exceeds the certified primal value";
-    case RELAX_ENOTSUP: return "shape or option not supported by this build";
+    case RELAX_ENOTSUP: return "shape or option not supported by this library";
     default: return "unknown status";
   }
 }
