@@ -79,7 +79,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
+def profile_traffic(workload=WORKLOAD):
     """DRAM bytes per X-pass launch from the committed ncu summary (its
     "key: value" lines), or None when the kernel source changed since the
     counters were taken."""
@@ -92,6 +92,8 @@ def profile_traffic():
     except Exception:
         return None
     if kv.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    if workload != WORKLOAD:        # the summary's counters are of the headline workload
         return None
     try:
         return float(kv["dram_bytes_per_launch_full"])
@@ -247,7 +249,7 @@ def run_ours(args):
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = profile_traffic()
+    traffic = profile_traffic(args.workload)
     value = throughput(args.steps, world, ms_max)
     line = {
         "metric": METRIC,
@@ -264,7 +266,7 @@ def run_ours(args):
         "data": "synthetic (seeded AR(1) Gaussian design, generated on the device)",
         "config": {"workload": args.workload, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2,
                    "rho": w.rho, "loss": w.loss, "M": w.M, "gap_tol": GAP_TOL, "snr": w.snr,
-                   "l2": "inputs larger than L2 (X is 4 GB), no flush",
+                   "l2": f"inputs larger than L2 (X is {w.n * w.p * 4 / 1e9:.1f} GB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_per_relaxation": iters,
         "certified_rel_gap": max(r.rel_gap for r in results),
