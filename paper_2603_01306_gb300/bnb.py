@@ -49,6 +49,7 @@ class BnBStats:
     certified: bool = False      # queue emptied: the incumbent is optimal
     seconds: float = 0.0
     pairs: list = field(default_factory=list)   # (parent beta, child fix, child beta) when recording
+    bounds: list = field(default_factory=list)  # (parent bound, child bound) of every child solved
 
 
 def _branch_var(beta, fix):
@@ -70,9 +71,11 @@ def _incumbent_fix(beta, fix, k):
     return f
 
 
-def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False, rel_tol=1e-9):
+def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False, rel_tol=1e-9, batch=1):
     """Best-first BnB on the handle's problem; stops when the queue empties
-    (certified) or after max_nodes relaxations."""
+    (certified) or after max_nodes relaxations.  batch > 1: up to `batch` open
+    nodes are taken in best-first order and all their children are solved in
+    one relax_solve_batch call (each warm-started like a single child)."""
     import torch
     dev = h.X.device
     st = BnBStats()
@@ -107,6 +110,13 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
     heap = [Node(res.dual_bound, 0, root, beta, res.iters)]
     try_incumbent(beta.double().cpu().numpy(), root)
     seq = 1
+    if batch > 1:
+        _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned,
+                     try_incumbent, dev)
+        st.certified = not heap
+        st.best_bound = min([n.bound for n in heap], default=st.incumbent)
+        st.seconds = time.perf_counter() - t0
+        return st
     while heap and st.nodes < max_nodes:
         node = heapq.heappop(heap)
         tol = rel_tol * max(1.0, abs(st.incumbent))
@@ -129,6 +139,7 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
                 break
             start = learned(node.beta, f) if warm == "learned" else node.beta
             beta, res, code = solve(f, start)
+            st.bounds.append((node.bound, res.dual_bound))
             if record:
                 st.pairs.append((node.beta.clone(), f.copy(), beta.clone()))
             if code not in (0, 4):
@@ -141,6 +152,59 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
     st.best_bound = min([n.bound for n in heap], default=st.incumbent)
     st.seconds = time.perf_counter() - t0
     return st
+
+
+def _children(node, k):
+    """The fixings of a node's children: its branching coordinate to J0 and,
+    while |J1| < k, to J1 (none when no free coordinate is nonzero)."""
+    j = _branch_var(node.beta.double().cpu().numpy(), node.fix)
+    if j < 0:
+        return []
+    f0 = node.fix.copy()
+    f0[j] = -1
+    kids = [f0]
+    if int(np.sum(node.fix > 0)) < k:
+        f1 = node.fix.copy()
+        f1[j] = 1
+        kids.append(f1)
+    return kids
+
+
+def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned, try_incumbent,
+                 dev):
+    import torch
+    seq = 1 << 30
+    while heap and st.nodes < max_nodes:
+        parents, kids = [], []
+        while heap and len(parents) < batch:
+            node = heapq.heappop(heap)
+            if node.bound >= st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
+                continue
+            for f in _children(node, k):
+                parents.append(node)
+                kids.append(f)
+        room = max_nodes - st.nodes
+        if not kids:
+            continue
+        parents, kids = parents[:room], kids[:room]
+        fixd = torch.tensor(np.stack(kids), device=dev)
+        starts = [learned(p.beta, f) if warm == "learned" else p.beta for p, f in zip(parents, kids)]
+        warmd = torch.stack([s.to(h.dtype) for s in starts]).contiguous()
+        betas, res, code = h.solve_batch(len(kids), fixings=fixd, warm_start=warmd, gap_tol=gap_tol)
+        for i, (p, f) in enumerate(zip(parents, kids)):
+            r = res[i]
+            st.nodes += 1
+            st.iters += r.iters + r.polish_iters
+            b = betas[i].clone()
+            st.bounds.append((p.bound, r.dual_bound))
+            if record:
+                st.pairs.append((p.beta.clone(), f.copy(), b))
+            if r.status not in (0, 4):
+                continue
+            if r.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
+                heapq.heappush(heap, Node(r.dual_bound, seq, f, b, r.iters))
+                seq += 1
+                try_incumbent(b.double().cpu().numpy(), f)
 
 
 def learned_start(h, net, parent_beta, fixings):

@@ -1,0 +1,39 @@
+"""The branch-and-bound driver on the GPU: children solved one at a time and
+children of up to 16 open nodes solved together in one batched call.  A
+child's feasible set is inside its parent's, so its relaxation bound is at
+least the parent's (up to the certified gap of the two solves); every
+incumbent is a feasible value, so no open bound exceeds it by more than the
+same tolerance."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_sequential_and_batched_bnb(lib):
+    from paper_2603_01306_gb300 import bnb
+    w = synth.Workload("bb", 800, 2000, 0.8, 15, 0.2, "ls")
+    X, y = synth.make_problem_cpu(w)
+    h = lib.Handle(torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), loss="ls", k=w.k,
+                   lambda2=w.lambda2, M=w.M)
+    runs = {}
+    for batch in (1, 16):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = bnb.run(h, w.k, max_nodes=97, gap_tol=1e-6, batch=batch)
+        torch.cuda.synchronize()
+        runs[batch] = (st, time.perf_counter() - t0)
+    h.close()
+    for batch, (st, secs) in runs.items():
+        assert st.nodes == 97
+        assert len(st.bounds) == st.nodes - 1                  # every child, not the root
+        for pb, cb in st.bounds:
+            assert cb >= pb - 2e-6 * max(1.0, abs(pb)), (batch, pb, cb)
+        assert st.best_bound <= st.incumbent * (1 + 2e-6)
+        print(f"batch {batch}: {st.nodes} nodes in {secs:.2f} s ({st.nodes / secs:.1f} nodes/s), "
+              f"iterations {st.iters}, incumbent {st.incumbent:.6f}, best open bound {st.best_bound:.6f}")
