@@ -93,3 +93,34 @@ def test_full_size_pass_and_certificate(lib):
     assert res.primal == pytest.approx(phi, rel=1e-6)
     assert res.dual_bound >= psi - 1e-6 * abs(psi)
     assert res.dual_bound <= phi + 1e-9 * abs(phi)
+
+
+def test_full_size_batch_certificates(lib):
+    """256 nodes sharing X 5000 x 10000 (the batched configuration): every node
+    certifies rel. gap 1e-6, and for 6 sampled nodes the oracle's Phi and Psi
+    at the returned beta under that node's fixings bracket the bound."""
+    w = synth.WORKLOADS["batch256_5000x10000_f32"]
+    nb = w.extra["nodes"]
+    X, y = synth.make_problem_gpu(w)
+    fix = np.stack([synth.node_fixings(w.p, 0, j, w.extra["j0_max"], w.extra["j1_max"], k=w.k) for j in range(nb)])
+    h = lib.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M)
+    betas, res, code = h.solve_batch(nb, fixings=torch.tensor(fix, device="cuda"), gap_tol=1e-6)
+    torch.cuda.synchronize()
+    h.close()
+    assert code == 0, lib.STATUS[code]
+    assert all(r.status == 0 and r.rel_gap <= 1e-6 for r in res)
+    Xh = X.cpu().numpy()
+    yh = y.double().cpu().numpy()
+    for j in (0, 1, 57, 128, 200, 255):
+        b = betas[j].double().cpu().numpy()
+        assert np.all(b[fix[j] < 0] == 0.0)
+        zb = _xv(Xh, b)
+        phi = losses.F(zb, yh, w.loss) + 2.0 * w.lambda2 * regularizer.g_alg1(b, fix[j], w.k, w.M, domain_rtol=1e-6)
+        zeta = -losses.grad_F(zb, yh, w.loss)
+        wv = _xtv(Xh, zeta)
+        psi = (-losses.F_conj(-zeta, yh, w.loss)
+               - 2.0 * w.lambda2 * regularizer.gstar(wv / (2.0 * w.lambda2), fix[j], w.k, w.M))
+        r = res[j]
+        assert np.isfinite(phi) and np.isfinite(psi), j
+        assert r.primal == pytest.approx(phi, rel=1e-6), j
+        assert psi - 1e-6 * abs(psi) <= r.dual_bound <= phi + 1e-9 * abs(phi), (j, psi, r.dual_bound, phi)
