@@ -103,6 +103,8 @@ typedef struct {
   int32_t stalled;     /* 1: the loop stopped on the stall rule (see stall_window) */
   int32_t polish_iters; /* relax_solve_batch: iterations of the single-node finish that a
                           node stalled in the batch received (0: none) */
+  int32_t cutoff_rule; /* dynamic termination (relax_set_cutoff): 0 none, 1 the loop's Phi
+                          fell to the cutoff (branch), 2 its Psi reached it (prune) */
 } relax_result;
 
 /* Create a solver handle bound to one design X and response y (Sec. 2.3).
@@ -163,6 +165,15 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
 relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixings,
                                const void* warm_start, double gap_tol, void* beta_out,
                                relax_result* out);
+
+/* Dynamic termination of Sec. 5.3 for the handle's later solves (single and
+ * batched): with cutoff = f(X b) + lambda2 ||b||^2 of the incumbent b, a
+ * node's loop stops as soon as its Phi falls to the cutoff (the node will be
+ * branched: result.cutoff_rule = 1) or its Psi reaches it (the node can be
+ * pruned: cutoff_rule = 2).  Such a solve is RELAX_OK whatever its gap; the
+ * certified bound is valid as always.  cutoff = +inf turns it off (the
+ * default); NaN is RELAX_EINVAL. */
+relax_status relax_set_cutoff(relax_handle* h, double cutoff);
 
 /* One fused pass over X (the matrix-vector products of Sec. 5.2.3 that dominate
  * the method): z = X beta, r = grad F(z), g = X' r, read of X once.

@@ -15,7 +15,8 @@ RELAX_F64, RELAX_F32, RELAX_BF16, RELAX_FP8E4M3 = 0, 1, 2, 3
 STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA", 4: "RELAX_ENOTCONV",
           5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
 
-EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_xpass", "relax_certify", "relax_destroy",
+EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_set_cutoff", "relax_xpass", "relax_certify",
+           "relax_destroy",
            "prox_persp", "prox_persp_noalloc", "gval_persp", "gstar_persp",
            "relax_mlp_features", "relax_mlp_forward", "relax_mlp_grad", "relax_mlp_adam",
            "relax_strerror", "relax_error_detail"]
@@ -46,7 +47,8 @@ class Result(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("n_nz", ctypes.c_int32), ("launches", ctypes.c_int32), ("xpass_count", ctypes.c_int32),
                 ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double),
-                ("stalled", ctypes.c_int32), ("polish_iters", ctypes.c_int32)]
+                ("stalled", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
+                ("cutoff_rule", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -73,6 +75,7 @@ def load():
                                  ctypes.POINTER(Options), vp]
     lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
     lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_set_cutoff.argtypes = [vp, dbl]
     lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
     lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_destroy.argtypes = [vp]
@@ -332,6 +335,10 @@ class Handle:
         g = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
         loss = relax_xpass(self.h, beta, z, g)
         return z, g, loss
+
+    def set_cutoff(self, cutoff=float("inf")):
+        """Dynamic termination against the incumbent's objective (inf: off)."""
+        _check(load().relax_set_cutoff(self.h, float(cutoff)), "relax_set_cutoff")
 
     def mlp_features(self, beta_parent, fixings=None, out=None):
         """(p, 5) float32 features of a child node (include/warmstart.h)."""

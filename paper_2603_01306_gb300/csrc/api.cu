@@ -217,6 +217,7 @@ struct relax_handle {
   double M = 2.0, eta = 0.0;
   int max_iters = 100000, chunk = 32;
   int stall_min = 1000;      // least window of the stall rule (0: off)
+  double cutoff = INFINITY;  // incumbent objective for the dynamic termination (inf: off)
   uint64_t limit_ns = 4000000000ull;
   bool certify = true;
   double L = 0.0;
@@ -330,6 +331,8 @@ PArgs base_pargs(relax_handle* h) {
   a.eta = h->eta;
   a.max_iters = h->max_iters;
   a.stall_min = h->stall_min;
+  a.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
+  a.cutoff = h->cutoff;
   a.lossp = nullptr;
   a.acc = h->acc;
   a.bpart = h->bpart;
@@ -973,7 +976,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     cert_dual = psi;
     const double crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
     if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel) || quantized ||
-        S0.stalled || crel > 0.9 * prev_crel)
+        S0.stalled || S0.cut_rule || crel > 0.9 * prev_crel)
       break;
     prev_crel = crel;
     ++cert_rounds;
@@ -1007,6 +1010,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   }
   out->restarts = S.restarts;
   out->stalled = S.stalled;
+  out->cutoff_rule = S.cut_rule;
   out->primal_loop = S.phi_best;
   out->dual_loop = S.psi_best;
   out->primal = have_cert ? cert_primal : S.phi_best;
@@ -1026,11 +1030,17 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     if (!std::isfinite(out->dual_bound) || std::isnan(out->primal)) status = RELAX_ENUMERIC;
     else if (out->dual_bound > out->primal + 1e-9 * std::max(1.0, std::fabs(out->primal)))
       status = RELAX_EINVALID_BOUND;
-    else if (!(out->rel_gap <= gap_tol))   // the certified gap when certification ran
+    else if (!(out->rel_gap <= gap_tol) && !S.cut_rule)   // the certified gap when certification ran
       status = RELAX_ENOTCONV;
   }
   out->status = status;
   return status;
+}
+
+relax_status relax_set_cutoff(relax_handle* h, double cutoff) {
+  if (!h || std::isnan(cutoff)) return RELAX_EINVAL;
+  h->cutoff = cutoff;
+  return RELAX_OK;
 }
 
 relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g_out, double* loss_host) {
@@ -1544,11 +1554,12 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
                                                          static_cast<unsigned char*>(beta_out) + es * (size_t)p * j,
                                                          f64 ? 1 : 0, p);
     o.stalled = S.stalled;
+    o.cutoff_rule = S.cut_rule;
     auto judge = [&](relax_status s0) {
       if (s0 != RELAX_OK) return s0;
       if (!std::isfinite(o.dual_bound) || std::isnan(o.primal)) return RELAX_ENUMERIC;
       if (o.dual_bound > o.primal + 1e-9 * std::max(1.0, std::fabs(o.primal))) return RELAX_EINVALID_BOUND;
-      if (!(o.rel_gap <= gap_tol)) return RELAX_ENOTCONV;
+      if (!(o.rel_gap <= gap_tol) && !o.cutoff_rule) return RELAX_ENOTCONV;
       return RELAX_OK;
     };
     st_j = judge(st_j);

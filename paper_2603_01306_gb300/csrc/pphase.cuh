@@ -75,6 +75,7 @@ struct IterState {
   double stall_gap;             // best gap when it last fell by 10%
   int stall_iter;               // iteration of that fall
   int stalled;                  // 1: the loop stopped on the stall rule
+  int cut_rule;                 // dynamic termination of Sec. 5.3: 1 Phi <= cutoff, 2 Psi >= cutoff
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
 
@@ -86,6 +87,8 @@ struct PArgs {
   double lambda2, M, step, rho, eta, tol;
   int max_iters;
   int stall_min;                // stall rule's least window (0: off)
+  int cutoff_on;                // dynamic termination against `cutoff` (0: off)
+  double cutoff;                // the incumbent's objective f(X b) + lambda2 ||b||^2
   const int8_t* fix;            // NULL = root
   const void* part;             // [ncl][NB][p] doubles
   int ncl, NB;
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
 
   bool stop = false, restart = false, imp_p = false, imp_d = false;
   double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
-  int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0;
+  int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0, cut_rule = 0;
   double stall_gap = 0.0;
   const int t = st ? st->iter : 0;
   if (mode == PM_ITER) {
@@ -606,6 +609,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     } else if (a.stall_min > 0 && t - stall_iter >= max(a.stall_min, t / 4)) {
       stop = true;
       stalled = 1;
+    }
+    // Dynamic termination (Sec. 5.3): once Phi falls to the incumbent's
+    // objective the node will not be pruned, so branch now; once Psi reaches
+    // it the node is pruned.  Pruning wins when both hold.
+    if (a.cutoff_on) {
+      if (isfinite(phi_best) && phi_best <= a.cutoff) { stop = true; cut_rule = 1; }
+      if (psi_best >= a.cutoff) { stop = true; cut_rule = 2; }
     }
   }
 
@@ -809,6 +819,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         st->stall_gap = stall_gap;
         st->stall_iter = stall_iter;
         st->stalled = stalled;
+        st->cut_rule = cut_rule;
         if (stop) {
           st->done = 1;
           st->ps.done = 1;

@@ -206,3 +206,37 @@ def test_stall_rule_ends_a_solve_below_the_fp32_floor(lib, loss):
     assert res.iters < 20000, (res.iters, res.stalled)
     assert res.dual_bound <= opt + 1e-12 * abs(opt)
     assert res.dual_bound == pytest.approx(opt, rel=1e-6)
+
+
+def test_dynamic_termination_rules(lib):
+    """Sec. 5.3's dynamic termination against an incumbent's objective: above
+    the node's optimum the loop stops once Phi falls to it (rule 1, branch);
+    below the optimum it stops once Psi reaches it (rule 2, prune), and the
+    certified bound then proves the pruning.  Off again, the solve is the
+    plain one.  In a batch every node follows the same rules."""
+    w = synth.Workload("cut", 300, 700, 0.7, 8, 0.5, "ls")
+    X, y = problem(w)
+    L = solver.lipschitz(X, "ls")
+    opt = solver.solve(X, y, "ls", w.k, w.lambda2, w.M, gap_tol=1e-12, L=L, max_iters=200000).dual_bound
+    h = lib.Handle(torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), loss="ls", k=w.k,
+                   lambda2=w.lambda2, M=w.M, lipschitz=L)
+    _, r0, c0 = h.solve(gap_tol=1e-10)
+    assert c0 == 0 and r0.cutoff_rule == 0
+    h.set_cutoff(1.05 * opt)
+    _, r1, c1 = h.solve(gap_tol=1e-10)
+    assert c1 == 0 and r1.cutoff_rule == 1 and r1.iters < r0.iters
+    assert r1.primal <= 1.05 * opt * (1 + 1e-9) and r1.dual_bound <= opt + 1e-12 * abs(opt)
+    h.set_cutoff(0.95 * opt)
+    _, r2, c2 = h.solve(gap_tol=1e-10)
+    assert c2 == 0 and r2.cutoff_rule == 2 and r2.iters < r0.iters
+    assert 0.95 * opt * (1 - 1e-9) <= r2.dual_bound <= opt + 1e-12 * abs(opt)
+    nb = 4
+    fix = np.stack([synth.node_fixings(w.p, 7, j, 40, 5, k=w.k) for j in range(nb)])
+    _, rb, cb = h.solve_batch(nb, fixings=torch.tensor(fix, device="cuda"), gap_tol=1e-10)
+    assert cb == 0
+    for r in rb:                      # every node's optimum is at least the root's
+        assert r.cutoff_rule == 2 and r.dual_bound >= 0.95 * opt * (1 - 1e-9)
+    h.set_cutoff()
+    _, r3, c3 = h.solve(gap_tol=1e-10)
+    assert c3 == 0 and r3.cutoff_rule == 0 and r3.iters == r0.iters
+    h.close()
