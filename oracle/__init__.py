@@ -18,9 +18,11 @@ written from the paper's definitions and algorithms:
   tiny p, and the ridge closed form.
 * ``mlp``: the per-coordinate warm-start network (forward, MSE gradient by the
   chain rule, Adam, BF16 rounding) and its input features.
+* ``variants``: the methods of the convergence study (Sec. 5.2): PGD and FISTA,
+  fixed step or backtracking, gap / function-value / no restart.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` and ``tests/test_oracle_mlp.py`` (worked examples, closed forms, Fenchel-Young
+``tests/test_oracle_pins.py``, ``tests/test_oracle_mlp.py`` and ``tests/test_oracle_variants.py`` (worked examples, closed forms, Fenchel-Young
 equalities, brute force); none is "parity unpinned".
 """
-from . import regularizer, losses, solver, brute, mlp  # noqa: F401
+from . import regularizer, losses, solver, brute, mlp, variants  # noqa: F401
