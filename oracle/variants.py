@@ -28,9 +28,12 @@ from .solver import Result, dual, induced_dual, lipschitz, primal
 
 
 def solve(X, y, loss, k, lambda2, M=2.0, fix=None, warm=None, gap_tol=1e-6, method="fista", step="fixed",
-          restart="gap", eta=math.e ** 3, L=None, max_iters=100000, record=False):
+          restart="gap", eta=math.e ** 3, L=None, max_iters=100000, record=False, cutoff=None):
     """Returns solver.Result; with record, history rows are
-    (t, Phi_t, Psi_t, restarted, L_t)."""
+    (t, Phi_t, Psi_t, restarted, L_t).  cutoff (the incumbent's objective)
+    adds the dynamic termination of Sec. 5.3: stop once Phi(beta^t) <= cutoff
+    (the node will be branched) or Psi(zeta^t) >= cutoff (it is pruned); the
+    rule that fired is returned as result.cutoff_rule (1 or 2, 0 none)."""
     if method not in ("fista", "pgd") or step not in ("fixed", "backtracking") or \
             restart not in ("gap", "function", "none"):
         raise ValueError("unknown method, step rule or restart")
@@ -66,8 +69,9 @@ def solve(X, y, loss, k, lambda2, M=2.0, fix=None, warm=None, gap_tol=1e-6, meth
 
     x_prev, yk, t = x0, x0, 1.0
     it = restarts = 0
+    cut_rule = 0
     converged = done()
-    while not converged and it < max_iters:
+    while not converged and not cut_rule and it < max_iters:
         it += 1
         Fy, grad = F_and_grad(yk)
         if step == "fixed":
@@ -111,6 +115,13 @@ def solve(X, y, loss, k, lambda2, M=2.0, fix=None, warm=None, gap_tol=1e-6, meth
         x_prev = x
         phi_prev = phi
         converged = done()
+        if cutoff is not None:
+            if phi <= cutoff:
+                cut_rule = 1
+            if psi >= cutoff:
+                cut_rule = 2
     gap = best_phi - best_psi
-    return Result(best_beta, best_phi, best_psi, gap, gap / max(1.0, abs(best_phi)), it, restarts, converged,
-                  hist, x_prev)
+    res = Result(best_beta, best_phi, best_psi, gap, gap / max(1.0, abs(best_phi)), it, restarts, converged,
+                 hist, x_prev)
+    res.cutoff_rule = cut_rule
+    return res

@@ -85,3 +85,21 @@ def test_unknown_options_are_rejected():
     w, X, y = _problem("ls")
     with pytest.raises(ValueError):
         variants.solve(X, y, "ls", w.k, w.lambda2, w.M, method="acfgm")
+
+
+def test_dynamic_termination_rules_of_the_oracle():
+    """Sec. 5.3: above the optimum the loop stops at the first iterate whose
+    Phi is at most the cutoff; below it, at the first whose Psi reaches it,
+    with that Psi as a bound proving the pruning.  Both stop before the full
+    solve does."""
+    w, X, y = _problem("ls", seed=5)
+    full = variants.solve(X, y, "ls", w.k, w.lambda2, w.M, gap_tol=1e-10, record=True)
+    opt = full.dual_bound
+    up = variants.solve(X, y, "ls", w.k, w.lambda2, w.M, gap_tol=1e-10, cutoff=1.05 * opt, record=True)
+    assert up.cutoff_rule == 1 and up.iters < full.iters
+    first = next(h[0] for h in full.history if h[1] <= 1.05 * opt)     # same iterates until the stop
+    assert up.iters == first
+    down = variants.solve(X, y, "ls", w.k, w.lambda2, w.M, gap_tol=1e-10, cutoff=0.95 * opt, record=True)
+    assert down.cutoff_rule == 2 and down.iters < full.iters
+    assert 0.95 * opt <= down.dual_bound <= opt * (1 + 1e-12)
+    assert variants.solve(X, y, "ls", w.k, w.lambda2, w.M, gap_tol=1e-10).cutoff_rule == 0
