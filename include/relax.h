@@ -155,10 +155,13 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
  *   out: host relax_result[nb], filled per node.
  * Per iteration the active nodes' points are the columns of a matrix B;
  * Z = X B and G = X' R run as two GEMMs (FP32 X: FP32 emulated on the BF16
- * tensor cores; FP64 X: FP64), and each node's prox / g / g* / gap / restart
- * step runs in its own segment of one launch.  Nodes converge after uneven
- * iteration counts and leave the batch every 16 iterations.  Each node's bound
- * is certified in FP64 as in relax_solve (without resuming).  Needs FP32 or
+ * tensor cores from 32 active nodes on, plain FP32 below; FP64 X: FP64), and
+ * each node's prox / g / g* / gap / restart step runs in its own segment of
+ * one launch.  Nodes converge after uneven iteration counts and leave the
+ * batch every 16 iterations; the stall rule's window is at most 200 inside a
+ * batch, and a node that stalls above gap_tol is finished by relax_solve's
+ * loop from its best point (out[j].polish_iters).  Each node's bound is
+ * certified in FP64 as in relax_solve (without resuming).  Needs FP32 or
  * FP64 storage of X (RELAX_ENOTSUP for BF16/FP8).  Returns RELAX_OK when every
  * node certified gap_tol, else the first failing node's status (out[j].status
  * holds each node's).  Synchronizes the handle's stream. */

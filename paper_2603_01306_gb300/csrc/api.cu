@@ -1186,10 +1186,12 @@ void set_error_detail(const char* msg) { snprintf(g_detail, sizeof(g_detail), "%
 // ======================================================= batched node solves
 // Many node relaxations of one design in lockstep: per iteration the active
 // nodes' points form the columns of B, Z = X B and G = X' R are two GEMMs
-// (FP32 data: FP32 emulated on the BF16 tensor cores; FP64: FP64), and the
-// p-phase of every active node runs in one segmented launch (waves when the
-// nodes' CTAs exceed what can be co-resident).  Converged nodes leave the
-// active set every kRetire iterations.
+// (FP32 data: FP32 emulated on the BF16 tensor cores from kEmulateMin columns
+// on, plain FP32 below; FP64: FP64), and the p-phase of every active node runs
+// in one segmented launch (one thread-block cluster per node, or cooperative
+// waves when p needs more CTAs than a cluster holds).  Converged nodes leave
+// the active set every kRetire iterations; a node stalled on the products'
+// floor is finished by the single-node loop.
 namespace {
 
 constexpr int kRetire = 16;
