@@ -165,6 +165,12 @@ WORKLOADS = {
     "bnb_2000x5000_f32": Workload("bnb_2000x5000_f32", 2000, 5000, 0.8, 15, 0.2, "ls",
                                   5.0),
 }
+# The root-relaxation sweep of Sec. 5.2: n = p in {1000, ..., 16000}, rho 0.5,
+# k 10, M 2, lambda2 1, SNR 5 (least squares and logistic), FP32 data.
+for _p in (1000, 2000, 4000, 8000, 16000):
+    for _loss in ("ls", "logistic"):
+        _name = f"paper_{_loss}_{_p}x{_p}_f32"
+        WORKLOADS[_name] = Workload(_name, _p, _p, 0.5, 10, 1.0, _loss, 5.0)
 
 
 def make_problem_cpu(w: Workload, n: int | None = None, p: int | None = None,

@@ -57,3 +57,13 @@ def test_support_and_fixings():
     f = synth.node_fixings(10000, 0, 5, 40, 19, k=20)
     assert np.sum(f < 0) <= 40 and np.sum(f > 0) <= 19
     assert np.array_equal(f, synth.node_fixings(10000, 0, 5, 40, 19, k=20))
+
+
+def test_paper_sweep_workloads():
+    # Sec. 5.2's root-relaxation sweep: n = p, rho 0.5, k 10, M 2, lambda2 1
+    for p in (1000, 2000, 4000, 8000, 16000):
+        for loss in ("ls", "logistic"):
+            w = synth.WORKLOADS[f"paper_{loss}_{p}x{p}_f32"]
+            assert (w.n, w.p, w.rho, w.k, w.M, w.lambda2, w.loss) == (p, p, 0.5, 10, 2.0, 1.0, loss)
+    X, y = synth.make_problem_cpu(synth.WORKLOADS["paper_logistic_1000x1000_f32"])
+    assert X.shape == (1000, 1000) and set(np.unique(y)) <= {-1.0, 1.0}
