@@ -178,6 +178,15 @@ relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixing
  * default); NaN is RELAX_EINVAL. */
 relax_status relax_set_cutoff(relax_handle* h, double cutoff);
 
+/* Diagnostic of the failure detection: one block takes the library's grid
+ * barrier expecting a partner that never arrives, so its bounded wait must
+ * give up after watchdog_ms (1..60000) and record a timeout, as every device
+ * wait of the library does when its bound expires.  Returns RELAX_ETIMEOUT
+ * when it did, with the wait's device time in *waited_ms (host double, or
+ * NULL).  No GPU fault, no copy in flight; the context stays usable.
+ * Synchronizes `stream`. */
+relax_status relax_watchdog_probe(int32_t watchdog_ms, double* waited_ms, void* stream);
+
 /* One fused pass over X (the matrix-vector products of Sec. 5.2.3 that dominate
  * the method): z = X beta, r = grad F(z), g = X' r, read of X once.
  *   beta: device p (handle dtype), z_out: device n (handle dtype),

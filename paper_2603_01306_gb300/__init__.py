@@ -10,5 +10,5 @@ from .binding import (  # noqa: F401
     RelaxError, Options, Result, Handle, load, lib_path, exported_symbols,
     relax_create, relax_solve, relax_xpass, relax_certify, relax_destroy,
     prox_persp, prox_persp_noalloc, gval_persp, gstar_persp, relax_strerror, relax_error_detail, STATUS,
-    relax_mlp_forward, relax_mlp_grad, relax_mlp_adam, MLP_NTRAIN, MLP_NPARAM,
+    relax_mlp_forward, relax_mlp_grad, relax_mlp_adam, MLP_NTRAIN, MLP_NPARAM, relax_watchdog_probe,
 )

@@ -16,7 +16,7 @@ STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA",
           5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
 
 EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_set_cutoff", "relax_xpass", "relax_certify",
-           "relax_destroy",
+           "relax_destroy", "relax_watchdog_probe",
            "prox_persp", "prox_persp_noalloc", "gval_persp", "gstar_persp",
            "relax_mlp_features", "relax_mlp_forward", "relax_mlp_grad", "relax_mlp_adam",
            "relax_strerror", "relax_error_detail"]
@@ -76,6 +76,7 @@ def load():
     lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
     lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_set_cutoff.argtypes = [vp, dbl]
+    lib.relax_watchdog_probe.argtypes = [i32, ctypes.POINTER(dbl), vp]
     lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
     lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_destroy.argtypes = [vp]
@@ -229,6 +230,15 @@ def _f32(*ts):
     for t in ts:
         if t is not None and (t.dtype != torch.float32 or not t.is_contiguous()):
             raise TypeError("warm-start network buffers are contiguous float32 tensors")
+
+
+def relax_watchdog_probe(watchdog_ms):
+    """(status code, device ms waited) of the bounded-wait diagnostic."""
+    waited = ctypes.c_double(0.0)
+    code = load().relax_watchdog_probe(int(watchdog_ms), ctypes.byref(waited), _stream())
+    if code not in (0, 5):
+        _check(code, "relax_watchdog_probe")
+    return code, waited.value
 
 
 def relax_destroy(h):

@@ -1037,6 +1037,50 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   return status;
 }
 
+// One CTA takes the library's grid barrier expecting a partner that never
+// arrives: the bounded wait must give up after limit_ns and record ST_TIMEOUT.
+__global__ void watchdog_probe_kernel(unsigned long long* counter, uint64_t limit_ns, int* status, int* ok) {
+  const bool passed = grid_barrier(counter, 2ull, limit_ns, status);
+  if (threadIdx.x == 0) *ok = passed ? 1 : 0;
+}
+
+relax_status relax_watchdog_probe(int32_t watchdog_ms, double* waited_ms, void* stream) {
+  if (watchdog_ms <= 0 || watchdog_ms > 60000) return RELAX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* buf = nullptr;
+  relax_status rs = alloc((void**)&buf, 64);
+  if (rs != RELAX_OK) return rs;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(buf);
+  int* status = reinterpret_cast<int*>(buf + 16);
+  int* ok = reinterpret_cast<int*>(buf + 32);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 64, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    watchdog_probe_kernel<<<1, 32, 0, st>>>(counter, (uint64_t)watchdog_ms * 1000000ull, status, ok);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  int hs[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs[0], status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs[1], ok, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_detail("watchdog probe", e, __LINE__);
+    return map_cuda(e);
+  }
+  if (waited_ms) *waited_ms = ms;
+  if (hs[1]) return RELAX_OK;                 // cannot happen: nobody else arrives
+  return map_dev_status(hs[0]);
+}
+
 relax_status relax_set_cutoff(relax_handle* h, double cutoff) {
   if (!h || std::isnan(cutoff)) return RELAX_EINVAL;
   h->cutoff = cutoff;

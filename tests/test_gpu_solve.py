@@ -240,3 +240,17 @@ def test_dynamic_termination_rules(lib):
     _, r3, c3 = h.solve(gap_tol=1e-10)
     assert c3 == 0 and r3.cutoff_rule == 0 and r3.iters == r0.iters
     h.close()
+
+
+def test_watchdog_probe_times_out_and_the_context_survives(lib):
+    """Failure detection without a fault: a wait on a partner that never
+    arrives ends by its bound with RELAX_ETIMEOUT, and the GPU context serves
+    a solve afterwards."""
+    code, ms = lib.relax_watchdog_probe(50)
+    assert code == 5, lib.STATUS[code]                # RELAX_ETIMEOUT
+    assert 50.0 <= ms < 2000.0, ms
+    w = synth.Workload("wd", 60, 120, 0.5, 4, 0.5, "ls")
+    X, y = problem(w)
+    L = solver.lipschitz(X, "ls")
+    _, res, c = gpu_solve(lib, X, y, "ls", w.k, w.lambda2, w.M, L, tol=1e-8)
+    assert c == 0
