@@ -213,7 +213,11 @@ relax_status relax_destroy(relax_handle* h);
  *   counts_out: device int32[2] or NULL: {n_top, n_nz} = free coordinates with
  *      z_j = 1 (placed before the pooled block of Algorithm 2) and nonzero free
  *      outputs.
- * Uses stream-ordered scratch (cudaMallocAsync) on `stream`; does not synchronize. */
+ * Uses stream-ordered scratch (cudaMallocAsync) on `stream`; does not synchronize,
+ * so a failure inside the kernel cannot change the returned status.  It shows
+ * in the outputs instead: a NaN or Inf in beta_in, or a bounded device wait
+ * that expired, makes beta_out all NaN (every coordinate the failing blocks
+ * own, all of them for a non-finite input) and counts_out {-1, -1}. */
 relax_status prox_persp(const void* beta_in, void* beta_out, int64_t p, double step,
                         int32_t k, double lambda2, double M, const int8_t* fixings,
                         int32_t dtype, int32_t* counts_out, void* stream);
@@ -236,13 +240,17 @@ relax_status prox_persp(const void* beta_in, void* beta_out, int64_t p, double s
  *   Every call shares the one array and leaves its contents behind (each call
  *   zeroes what it needs at its start): calls that overlap on the GPU, e.g. on
  *   two streams without ordering between them, race and give wrong results.
- *   Does not synchronize. */
+ *   Does not synchronize; failures inside the kernel show in the outputs as
+ *   for prox_persp (NaN in beta_out, counts_out {-1, -1}), since the next call
+ *   clears the array's status word. */
 relax_status prox_persp_noalloc(const void* beta_in, void* beta_out, int64_t p, double step,
                                 int32_t k, double lambda2, double M, const int8_t* fixings,
                                 int32_t dtype, int32_t* counts_out, void* stream);
 
 /* g_N(beta) (Eq. 5; value of Algorithm 1 / Thm 4.4) into out_host[0]; +inf when
- * beta is outside dom g_N (beyond a relative tolerance of 4 ulp of dtype).
+ * beta is outside dom g_N: a J0 coordinate nonzero, |beta_j| > M (1 + 1e-6), or
+ * sum_Jf |beta_j| > M kbar (1 + 1e-6) (the relative slack admits boundary points
+ * rounded to FP32 or FP64).
  *   beta: device p of dtype.  Synchronizes `stream`. */
 relax_status gval_persp(const void* beta, int64_t p, int32_t k, double M,
                         const int8_t* fixings, int32_t dtype, double* out_host,

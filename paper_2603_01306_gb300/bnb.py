@@ -15,6 +15,15 @@ and measures it against the parent warm start.
 * Warm start of a child: the parent's beta ("parent"), or the learned start
   b + f(x) of include/warmstart.h ("learned"), which falls back to the parent's
   when its certified primal value is not lower.
+* Dynamic termination (Sec. 5.3, early-termination rules 1-2), on by default:
+  each child is solved with the incumbent's objective as the handle's cutoff
+  (relax_set_cutoff), so its loop stops once Phi falls to it (the child will
+  be branched) or Psi reaches it (the child is pruned).  Incumbent solves run
+  without a cutoff, since they need the restricted optimum.
+* Certification: the run is certified only when the queue empties with no
+  subtree dropped.  A child left unsolved (max_nodes reached) or whose solve
+  failed keeps its parent's bound as the bound of its unexplored subtree, and
+  best_bound is the least bound over the queue and those subtrees.
 
 Every relaxation, pass and network evaluation runs in the CUDA library; this
 module keeps the queue.
@@ -46,7 +55,10 @@ class BnBStats:
     fallbacks: int = 0           # children where the parent start was kept
     incumbent: float = float("inf")
     best_bound: float = float("-inf")
-    certified: bool = False      # queue emptied: the incumbent is optimal
+    certified: bool = False      # queue emptied and nothing dropped: the incumbent is optimal
+    dropped: list = field(default_factory=list)   # parent bounds of children left unsolved or failed
+    cut_branch: int = 0          # children stopped by rule 1 (Phi <= incumbent)
+    cut_prune: int = 0           # children stopped by rule 2 (Psi >= incumbent)
     seconds: float = 0.0
     pairs: list = field(default_factory=list)   # (parent beta, child fix, child beta) when recording
     bounds: list = field(default_factory=list)  # (parent bound, child bound) of every child solved
@@ -71,22 +83,42 @@ def _incumbent_fix(beta, fix, k):
     return f
 
 
-def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False, rel_tol=1e-9, batch=1):
+def _finish(st, heap, t0):
+    st.certified = not heap and not st.dropped
+    st.best_bound = min([n.bound for n in heap] + list(st.dropped), default=st.incumbent)
+    st.best_bound = min(st.best_bound, st.incumbent)
+    st.seconds = time.perf_counter() - t0
+    return st
+
+
+def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False, rel_tol=1e-9, batch=1,
+        cutoff=True):
     """Best-first BnB on the handle's problem; stops when the queue empties
-    (certified) or after max_nodes relaxations.  batch > 1: up to `batch` open
-    nodes are taken in best-first order and all their children are solved in
-    one relax_solve_batch call (each warm-started like a single child)."""
+    (certified, unless a subtree was dropped) or after max_nodes relaxations.
+    batch > 1: up to `batch` open nodes are taken in best-first order and all
+    their children are solved in one relax_solve_batch call (each
+    warm-started like a single child).  cutoff: solve children with the
+    dynamic termination of Sec. 5.3 against the incumbent."""
     import torch
     dev = h.X.device
     st = BnBStats()
     t0 = time.perf_counter()
 
+    def set_cut(node):
+        h.set_cutoff(st.incumbent if (cutoff and node) else float("inf"))
+
+    def count_cut(res):
+        st.cut_branch += res.cutoff_rule == 1
+        st.cut_prune += res.cutoff_rule == 2
+
     def solve(fix, start, node=True):
         fx = torch.tensor(fix, device=dev)
+        set_cut(node)
         beta, res, code = h.solve(fixings=fx, warm_start=start, gap_tol=gap_tol)
         if node:
             st.nodes += 1
             st.iters += res.iters
+            count_cut(res)
         else:
             st.incumbent_solves += 1
         return beta, res, code
@@ -112,11 +144,9 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
     seq = 1
     if batch > 1:
         _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned,
-                     try_incumbent, dev)
-        st.certified = not heap
-        st.best_bound = min([n.bound for n in heap], default=st.incumbent)
-        st.seconds = time.perf_counter() - t0
-        return st
+                     try_incumbent, dev, set_cut, count_cut)
+        h.set_cutoff(float("inf"))
+        return _finish(st, heap, t0)
     while heap and st.nodes < max_nodes:
         node = heapq.heappop(heap)
         tol = rel_tol * max(1.0, abs(st.incumbent))
@@ -136,6 +166,7 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
             kids.append(f1)
         for f in kids:
             if st.nodes >= max_nodes:
+                st.dropped.append(node.bound)      # the sibling's subtree stays unexplored
                 break
             start = learned(node.beta, f) if warm == "learned" else node.beta
             beta, res, code = solve(f, start)
@@ -143,15 +174,14 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
             if record:
                 st.pairs.append((node.beta.clone(), f.copy(), beta.clone()))
             if code not in (0, 4):
+                st.dropped.append(node.bound)      # a failed solve proves nothing about the child
                 continue
             if res.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
                 heapq.heappush(heap, Node(res.dual_bound, seq, f, beta, res.iters))
                 seq += 1
                 try_incumbent(beta.double().cpu().numpy(), f)
-    st.certified = not heap
-    st.best_bound = min([n.bound for n in heap], default=st.incumbent)
-    st.seconds = time.perf_counter() - t0
-    return st
+    h.set_cutoff(float("inf"))
+    return _finish(st, heap, t0)
 
 
 def _children(node, k):
@@ -171,7 +201,7 @@ def _children(node, k):
 
 
 def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned, try_incumbent,
-                 dev):
+                 dev, set_cut, count_cut):
     import torch
     seq = 1 << 30
     while heap and st.nodes < max_nodes:
@@ -186,20 +216,26 @@ def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, he
         room = max_nodes - st.nodes
         if not kids:
             continue
+        # children beyond the node budget stay unexplored: their parents'
+        # bounds remain bounds of those subtrees
+        st.dropped.extend(p.bound for p in parents[room:])
         parents, kids = parents[:room], kids[:room]
         fixd = torch.tensor(np.stack(kids), device=dev)
         starts = [learned(p.beta, f) if warm == "learned" else p.beta for p, f in zip(parents, kids)]
         warmd = torch.stack([s.to(h.dtype) for s in starts]).contiguous()
+        set_cut(True)
         betas, res, code = h.solve_batch(len(kids), fixings=fixd, warm_start=warmd, gap_tol=gap_tol)
         for i, (p, f) in enumerate(zip(parents, kids)):
             r = res[i]
             st.nodes += 1
             st.iters += r.iters + r.polish_iters
+            count_cut(r)
             b = betas[i].clone()
             st.bounds.append((p.bound, r.dual_bound))
             if record:
                 st.pairs.append((p.beta.clone(), f.copy(), b))
             if r.status not in (0, 4):
+                st.dropped.append(p.bound)
                 continue
             if r.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
                 heapq.heappush(heap, Node(r.dual_bound, seq, f, b, r.iters))

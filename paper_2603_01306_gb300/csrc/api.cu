@@ -255,6 +255,16 @@ struct relax_handle {
   int* h_done = nullptr;         // pinned [2]
   double* h_d = nullptr;         // pinned doubles
   int* h_i = nullptr;            // pinned ints
+  // The single-node loop's chunk of `chunk` iterations, captured once as a
+  // CUDA graph and replayed by every later solve.  Its kernels read only
+  // handle-owned memory (state, buffers, the copy of the solve's fixings in
+  // fixbuf), so one graph serves every solve with the same shape of call:
+  // with or without fixings, with or without timing events.
+  int8_t* fixbuf = nullptr;      // device p: the current solve's fixings
+  cudaGraphExec_t gexec = nullptr;
+  int g_fix = -1, g_timing = -1; // what gexec was captured for (-1: nothing)
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // host polls of the loop
+  cudaEvent_t* tev = nullptr;    // [chunk][3] timing events recorded inside gexec
   size_t esz() const { return dtype == RELAX_F64 ? 8 : 4; }
   int f64() const { return dtype == RELAX_F64 ? 1 : 0; }
 };
@@ -274,6 +284,13 @@ void handle_free(relax_handle* h) {
   if (h->h_d) cudaFreeHost(h->h_d);
   if (h->h_i) cudaFreeHost(h->h_i);
   if (h->cublas) cublasDestroy(h->cublas);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (cudaEvent_t e : h->ev) if (e) cudaEventDestroy(e);
+  if (h->tev) {
+    for (int i = 0; i < 3 * h->chunk; ++i) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
+    delete[] h->tev;
+  }
+  if (h->fixbuf) cudaFree(h->fixbuf);
   delete h;
 }
 
@@ -331,8 +348,6 @@ PArgs base_pargs(relax_handle* h) {
   a.eta = h->eta;
   a.max_iters = h->max_iters;
   a.stall_min = h->stall_min;
-  a.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
-  a.cutoff = h->cutoff;
   a.lossp = nullptr;
   a.acc = h->acc;
   a.bpart = h->bpart;
@@ -779,6 +794,9 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(cudaHostAlloc((void**)&h->h_done, 2 * sizeof(int), cudaHostAllocDefault));
     TRYC(cudaHostAlloc((void**)&h->h_d, 1024 * sizeof(double), cudaHostAllocDefault));
     TRYC(cudaHostAlloc((void**)&h->h_i, 16 * sizeof(int), cudaHostAllocDefault));
+    TRY(alloc((void**)&h->fixbuf, (size_t)p));
+    TRYC(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+    TRYC(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
     if (o.lipschitz > 0.0) h->L = o.lipschitz;
     else TRY(power_iteration(h, &h->L));
     TRYC(cudaStreamSynchronize(h->stream));
@@ -839,21 +857,29 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.ps.zout = s.z_cur;
   s.ps.zprev = s.z_prev;
   s.ps.mom = 0.0;
+  s.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
+  s.cutoff = h->cutoff;
   *h->h_state = s;
   CU(cudaMemcpyAsync(h->st, h->h_state, sizeof(IterState), cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
   CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  // the loop reads the fixings from the handle's own copy, so that one
+  // captured graph serves every solve
+  const int8_t* fix_loop = nullptr;
+  if (fixings) {
+    CU(cudaMemcpyAsync(h->fixbuf, fixings, (size_t)h->p, cudaMemcpyDeviceToDevice, h->stream));
+    fix_loop = h->fixbuf;
+  }
   // ---- one iteration = fused X-pass + p-phase; enqueue `chunk` per host poll
   XSArgs xa = pass_args(h, h->pl_loop, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps);
   PArgs pa = base_pargs(h);
   pa.mode = PM_ITER;
-  pa.fix = fixings;
+  pa.fix = fix_loop;
   pa.part = h->xg;
   pa.ncl = h->pl_loop.Gr;
   pa.NB = h->pl_loop.NB;
   pa.st = h->st;
   pa.bar = h->bar;
-  pa.tol = gap_tol;
   pa.fast_s1 = h->dtype == RELAX_F32 ? 1 : 0;   // FP32-key top-k select only for FP32 data
   pa.lossp = nullptr;                          // loss terms from z^t (FP64, in the p-phase)
   pa.y = (const double*)h->y;
@@ -862,12 +888,12 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   // graph); the host then waits for each chunk before enqueueing the next.
   const bool timing = h->opt.timing != 0;
   const int chunk = h->chunk;
-  cudaEvent_t* tev = nullptr;   // [chunk][3]: before X-pass, after X-pass, after p-phase
-  if (timing) {
-    tev = new (std::nothrow) cudaEvent_t[(size_t)chunk * 3];
-    if (!tev) return RELAX_ENOMEM;
-    for (int i = 0; i < chunk * 3; ++i) cudaEventCreate(&tev[i]);
+  if (timing && !h->tev) {   // [chunk][3]: before X-pass, after X-pass, after p-phase
+    h->tev = new (std::nothrow) cudaEvent_t[(size_t)chunk * 3]();
+    if (!h->tev) return RELAX_ENOMEM;
+    for (int i = 0; i < chunk * 3; ++i) CU(cudaEventCreate(&h->tev[i]));
   }
+  cudaEvent_t* tev = h->tev;
   auto enqueue_body = [&](cudaStream_t cs) -> cudaError_t {
     for (int i = 0; i < chunk; ++i) {
       cudaError_t e;
@@ -879,9 +905,12 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     }
     return cudaSuccess;
   };
-  // capture the chunk as a graph (falls back to direct launches)
-  cudaGraphExec_t gexec = nullptr;
-  {
+  // capture the chunk as a graph once per shape of call (falls back to direct launches)
+  if (!h->gexec || h->g_fix != (fix_loop ? 1 : 0) || h->g_timing != (timing ? 1 : 0)) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
     cudaGraph_t graph = nullptr;
     cudaStream_t cs = nullptr;
     bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
@@ -889,19 +918,20 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     if (ok) {
       const bool lok = enqueue_body(cs) == cudaSuccess;
       ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && lok && graph;
-      if (ok) ok = cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+      if (ok) ok = cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
     }
     if (cs) cudaStreamDestroy(cs);
-    if (!ok) { gexec = nullptr; cudaGetLastError(); }
+    if (!ok) { h->gexec = nullptr; cudaGetLastError(); }
+    h->g_fix = fix_loop ? 1 : 0;
+    h->g_timing = timing ? 1 : 0;
   }
+  cudaGraphExec_t gexec = h->gexec;
   auto enqueue_chunk = [&]() -> cudaError_t {
     if (gexec) return cudaGraphLaunch(gexec, h->stream);
     return enqueue_body(h->stream);
   };
-  cudaEvent_t ev[2];
-  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  cudaEvent_t* ev = h->ev;
   const int64_t max_chunks = (int64_t)h->max_iters / chunk + 3;
   cudaError_t err = cudaSuccess;
   int64_t nchunks = 0;
@@ -989,14 +1019,10 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     it_before = S0.iter;
     run_loop(std::max<int64_t>(8, (int64_t)S0.iter / (2 * chunk) + 1));
   }
-  cudaEventDestroy(ev[0]);
-  cudaEventDestroy(ev[1]);
-  if (tev) {
-    for (int i = 0; i < chunk * 3; ++i) cudaEventDestroy(tev[i]);
-    delete[] tev;
+  if (err != cudaSuccess) {
+    set_detail("loop chunk launch", err, __LINE__);
+    return map_cuda(err);
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (err != cudaSuccess) return map_cuda(err);
   out->launches += (int)(nchunks * chunk * 2) + 1 + (fixings ? 1 : 0);   // loop + init (+ count)
   CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
   int dst = 0;
@@ -1417,6 +1443,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     s.kbar = h->k - j1[j];
     s.pbar = jf[j];
     s.tol = loop_tol;
+    s.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
+    s.cutoff = h->cutoff;
     s.ps.beta = s.beta_cur;
     s.ps.zout = s.z_cur;
     s.ps.zprev = s.z_prev;

@@ -76,6 +76,8 @@ struct IterState {
   int stall_iter;               // iteration of that fall
   int stalled;                  // 1: the loop stopped on the stall rule
   int cut_rule;                 // dynamic termination of Sec. 5.3: 1 Phi <= cutoff, 2 Psi >= cutoff
+  int cutoff_on;                // dynamic termination against `cutoff` (0: off)
+  double cutoff;                // the incumbent's objective f(X b) + lambda2 ||b||^2
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
 
@@ -87,8 +89,6 @@ struct PArgs {
   double lambda2, M, step, rho, eta, tol;
   int max_iters;
   int stall_min;                // stall rule's least window (0: off)
-  int cutoff_on;                // dynamic termination against `cutoff` (0: off)
-  double cutoff;                // the incumbent's objective f(X b) + lambda2 ||b||^2
   const int8_t* fix;            // NULL = root
   const void* part;             // [ncl][NB][p] doubles
   int ncl, NB;
@@ -613,9 +613,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // Dynamic termination (Sec. 5.3): once Phi falls to the incumbent's
     // objective the node will not be pruned, so branch now; once Psi reaches
     // it the node is pruned.  Pruning wins when both hold.
-    if (a.cutoff_on) {
-      if (isfinite(phi_best) && phi_best <= a.cutoff) { stop = true; cut_rule = 1; }
-      if (psi_best >= a.cutoff) { stop = true; cut_rule = 2; }
+    if (st->cutoff_on) {
+      if (isfinite(phi_best) && phi_best <= st->cutoff) { stop = true; cut_rule = 1; }
+      if (psi_best >= st->cutoff) { stop = true; cut_rule = 2; }
     }
   }
 
@@ -646,6 +646,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   float mmf[EPT];  // |v| rounded to FP32 (rounds)
   float ti[EPT];   // T^{-1}(|v|) in FP32: where coordinate j reaches z_j = 1
   double nzv = 0.0;
+  double nbad = 0.0;   // standalone prox: non-finite inputs (the output is then all NaN)
   if (do_prox) {
     const TV* vin = static_cast<const TV*>(a.vin);
     const TV muv = (TV)mu;
@@ -666,6 +667,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         v = y - sv * (TV)gyv;
       } else {
         v = vin[j];
+        if (!isfinite((double)v)) nbad += 1.0;
       }
       vv[e] = v;
       if (fx[e] == 0) {
@@ -683,12 +685,17 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   double c = 0.0;
   int n_top = 0, n_nz = 0;
   if (do_prox) {
-    gsum(&nzv, 1);
+    {
+      double nv[2] = {nzv, nbad};
+      gsum(nv, 2);
+      nzv = nv[0];
+      nbad = nv[1];
+    }
     bool s3 = false;
     KV lo3 = 0, hi3 = (KV)KeyOf<float>::kInf;
     double cmlo = nzv, cmhi = 0.0, ctlo = nzv, cthi = 0.0;   // #{m > lo}, #{m > hi}, same for T^-1
     if (kb <= 0) c = INFINITY;
-    else if (nzv <= (double)kb) c = 0.0;
+    else if (nzv <= (double)kb || nbad > 0.0) c = 0.0;   // no threshold search on a non-finite input
     else s3 = true;
     const double rhoM = rho * M;
     const double c3p = (mode == PM_ITER) ? st->c_last : 0.0;
@@ -732,7 +739,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       const bool regime_inside = (rhoM > clo && rhoM <= chi);
       if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
     }
-    if (kb > 0 && nzv > (double)kb) {
+    if (kb > 0 && nzv > (double)kb && nbad == 0.0) {
       // exact finishing on the bracket's piece, polished until stable
       const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
       double ccur = chi;
@@ -770,13 +777,18 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     TV* out = mode == PM_ITER ? static_cast<TV*>(st->beta_prev) : static_cast<TV*>(a.vout);
     const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
     double cnt[2] = {0, 0};
+    // Standalone prox: a non-finite input, or a bounded wait of this block
+    // that expired (its threshold then rests on incomplete sums), gives NaN
+    // outputs instead of silently wrong ones; the counts get a sentinel below.
+    const bool poison = mode == PM_PROX && (nbad > 0.0 || !alive);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
       if (j >= p) continue;
       const double v = (double)vv[e];
       double b;
-      if (fx[e] < 0) b = 0.0;
+      if (poison) b = __longlong_as_double(0x7ff8000000000000ll);
+      else if (fx[e] < 0) b = 0.0;
       else if (fx[e] > 0) b = fmin(fmax(v / (1.0 + rho), -M), M);
       else {
         const double m = fabs(v);
@@ -792,10 +804,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (mode == PM_PROX && a.counts) {
       gsum(cnt, 2);
       if (lbk == 0 && tid == 0) {
-        a.counts[0] = (int)cnt[0];
-        a.counts[1] = (int)cnt[1];
+        // any block's expired wait has recorded its status by now (a block that
+        // gives up stops arriving, so every later barrier expires too)
+        const bool failed = poison || !alive || *(volatile int*)a.status != ST_OK;
+        a.counts[0] = failed ? -1 : (int)cnt[0];
+        a.counts[1] = failed ? -1 : (int)cnt[1];
       }
     }
+    if (mode == PM_PROX && nbad > 0.0 && lbk == 0 && tid == 0) atomicCAS(a.status, ST_OK, ST_NUMERIC);
   }
 
   // ------------------------------------------------------------- epilogue

@@ -40,3 +40,105 @@ def test_parameter_block_layout_and_initial_network():
     F = np.random.default_rng(0).standard_normal((9, 5))
     out, _ = mlp.forward(th, F)
     assert np.all(out == 0)
+
+
+class _OracleHandle:
+    """A stand-in for the device handle with the same methods the driver
+    calls, solving each node with the FP64 oracle on the CPU (test
+    infrastructure only).  `fail` lists fixings (as bytes) whose solve
+    returns RELAX_ECUDA, a failure injected on the host."""
+
+    def __init__(self, X, y, k, lam2, M, fail=()):
+        import torch
+        self.X = torch.tensor(X)
+        self.Xn, self.y, self.k, self.lam2, self.M = X, y, k, lam2, M
+        self.p = X.shape[1]
+        self.dtype = torch.float64
+        self.cut = float("inf")
+        self.fail = set(fail)
+        self.cut_calls = []
+
+    def set_cutoff(self, c=float("inf")):
+        self.cut = c
+        self.cut_calls.append(c)
+
+    def solve(self, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
+        import types
+        import torch
+        from oracle import variants
+        fix = fixings.cpu().numpy()
+        warm = None if warm_start is None else warm_start.double().cpu().numpy()
+        cut = None if self.cut == float("inf") else self.cut
+        r = variants.solve(self.Xn, self.y, "ls", self.k, self.lam2, self.M, fix=fix, warm=warm,
+                           gap_tol=gap_tol, cutoff=cut)
+        code = 0 if (r.converged or r.cutoff_rule) else 4
+        if fix.tobytes() in self.fail:
+            code = 3
+        res = types.SimpleNamespace(primal=r.primal, dual_bound=r.dual_bound, iters=r.iters,
+                                    cutoff_rule=r.cutoff_rule, polish_iters=0, status=code)
+        return torch.tensor(r.beta), res, code
+
+
+def _tiny(seed=0):
+    import synth
+    X = synth.ar1_design(30, 7, 0.5, seed)
+    y = synth.response(synth.signal_from_design(X, 2), "ls", 4.0, seed)
+    return X, y
+
+
+def test_bnb_reaches_the_bruteforce_optimum_with_cutoffs():
+    """With every solve exact (oracle) the queue empties, the run is
+    certified and its incumbent is the k-sparse optimum by support
+    enumeration; children are solved with the incumbent as cutoff."""
+    from oracle import brute
+    from paper_2603_01306_gb300 import bnb
+    X, y = _tiny()
+    k, lam2, M = 2, 0.3, 2.0
+    h = _OracleHandle(X, y, k, lam2, M)
+    st = bnb.run(h, k, max_nodes=200, gap_tol=1e-9)
+    opt = brute.ksparse_opt(X, y, "ls", k, lam2, M)
+    assert st.certified and not st.dropped
+    assert st.incumbent == pytest.approx(opt, rel=1e-7)
+    assert st.best_bound == st.incumbent
+    assert any(c != float("inf") for c in h.cut_calls)     # children ran with the incumbent cutoff
+    assert h.cut == float("inf")                            # and the handle is left without one
+    st2 = bnb.run(_OracleHandle(X, y, k, lam2, M), k, max_nodes=200, gap_tol=1e-9, cutoff=False)
+    assert st2.certified and st2.incumbent == pytest.approx(opt, rel=1e-7)
+    assert st.cut_branch + st.cut_prune > 0 and st2.cut_branch + st2.cut_prune == 0
+
+
+def test_bnb_is_not_certified_when_a_child_solve_fails():
+    from paper_2603_01306_gb300 import bnb
+    X, y = _tiny(1)
+    k, lam2, M = 2, 0.3, 2.0
+    # find the first child the driver will solve: the root's branching coordinate to J0
+    probe = _OracleHandle(X, y, k, lam2, M)
+    import torch
+    b0, r0, _ = probe.solve(torch.zeros(7, dtype=torch.int8), gap_tol=1e-9)
+    j = bnb._branch_var(b0.numpy(), np.zeros(7, dtype=np.int8))
+    f0 = np.zeros(7, dtype=np.int8)
+    f0[j] = -1
+    h = _OracleHandle(X, y, k, lam2, M, fail=[f0.tobytes()])
+    st = bnb.run(h, k, max_nodes=200, gap_tol=1e-9)
+    assert not st.certified
+    assert st.dropped == [pytest.approx(r0.dual_bound)]     # the root's bound covers the lost subtree
+    assert st.best_bound <= r0.dual_bound
+
+
+@pytest.mark.parametrize("batch", [1, 4])
+def test_bnb_is_not_certified_when_the_node_budget_runs_out(batch):
+    from paper_2603_01306_gb300 import bnb
+    X, y = _tiny(2)
+    k, lam2, M = 3, 0.2, 2.0
+    h = _OracleHandle(X, y, k, lam2, M)
+    h.solve_batch = None   # the batched path is exercised below through a list of single solves
+
+    def solve_batch(nb, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
+        import torch
+        outs = [h.solve(fixings[i], warm_start[i], gap_tol) for i in range(nb)]
+        return torch.stack([o[0] for o in outs]), [o[1] for o in outs], 0
+    h.solve_batch = solve_batch
+    st = bnb.run(h, k, max_nodes=3, gap_tol=1e-9, batch=batch)
+    assert st.nodes <= 3
+    assert not st.certified
+    assert st.best_bound <= st.incumbent

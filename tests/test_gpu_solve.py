@@ -87,6 +87,36 @@ def test_trajectory_is_the_oracles(lib, loss):
 
 
 @pytest.mark.parametrize("loss", ["ls", "logistic"])
+def test_f32_trajectory_is_the_oracles(lib, loss):
+    """FP32 storage of X: after the same K steps from the same L, the iterate
+    matches the FP64 oracle's on the same FP32-rounded X element by element
+    within 1e-5 relative (the FP32 bar), each coordinate against the iterate's
+    largest magnitude as its floor.  The device keeps the loop vectors in FP64
+    and forms the products from FP32 X, so the differences are the products'
+    FP32 rounding carried through K steps."""
+    w = synth.Workload("traj32", 160, 400, 0.6, 8, 0.3, loss)
+    X, y = problem(w, dtype=np.float32)
+    X64, y64 = X.astype(np.float64), y.astype(np.float64)
+    L = solver.lipschitz(X64, loss)
+    fix = synth.node_fixings(400, 7, 0, 20, 3, k=8)
+    for K in (1, 3, 40, 120):
+        ref = solver.solve(X64, y64, loss, w.k, w.lambda2, w.M, fix=fix, gap_tol=1e-300, L=L,
+                           max_iters=K)
+        beta, res, code = gpu_solve(lib, X, y, loss, w.k, w.lambda2, w.M, L, fix=fix, tol=1e-300,
+                                    max_iters=K, certify=False)
+        assert code == 4      # RELAX_ENOTCONV: stopped by max_iters
+        assert res.iters == ref.iters == K
+        assert res.restarts == ref.restarts
+        scale = float(np.max(np.abs(ref.beta)))
+        np.testing.assert_allclose(beta, ref.beta, rtol=1e-5, atol=1e-5 * scale)
+        # the same support: a coordinate is zero on one side only where the
+        # other side is below the floor
+        flip = (beta != 0) != (ref.beta != 0)
+        assert np.all(np.abs(beta[flip]) + np.abs(ref.beta[flip]) <= 1e-5 * scale)
+        assert res.primal_loop == pytest.approx(ref.primal, rel=1e-6)
+
+
+@pytest.mark.parametrize("loss", ["ls", "logistic"])
 def test_node_fixings_and_warm_start(lib, loss):
     w = synth.Workload("node", 200, 400, 0.7, 8, 0.5, loss)
     X, y = problem(w)
@@ -240,6 +270,35 @@ def test_dynamic_termination_rules(lib):
     _, r3, c3 = h.solve(gap_tol=1e-10)
     assert c3 == 0 and r3.cutoff_rule == 0 and r3.iters == r0.iters
     h.close()
+
+
+@pytest.mark.parametrize("loss", ["ls", "logistic"])
+@pytest.mark.parametrize("factor,rule", [(1.02, 1), (0.98, 2)])
+def test_cutoff_stop_is_the_oracles(lib, loss, factor, rule):
+    """The dynamic termination of Sec. 5.3 stops the device loop at the same
+    iterate as the oracle's (oracle.variants.solve with the same cutoff, FP64,
+    same L): the first iterate whose Phi falls to the cutoff (rule 1) or
+    whose Psi reaches it (rule 2), with the same best point and values."""
+    from oracle import variants
+    w = synth.Workload("cutpar", 150, 320, 0.6, 6, 0.4, loss)
+    X, y = problem(w)
+    L = solver.lipschitz(X, loss)
+    fix = synth.node_fixings(320, 5, 1, 15, 2, k=6)
+    opt = solver.solve(X, y, loss, w.k, w.lambda2, w.M, fix=fix, gap_tol=1e-12, L=L,
+                       max_iters=200000).dual_bound
+    cut = factor * opt
+    ref = variants.solve(X, y, loss, w.k, w.lambda2, w.M, fix=fix, gap_tol=1e-300, L=L, cutoff=cut)
+    assert ref.cutoff_rule == rule
+    h = lib.Handle(torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda"), loss=loss, k=w.k,
+                   lambda2=w.lambda2, M=w.M, lipschitz=L, certify=False)
+    h.set_cutoff(cut)
+    beta, res, code = h.solve(fixings=torch.tensor(fix, device="cuda"), gap_tol=1e-300)
+    h.close()
+    assert code == 0 and res.cutoff_rule == rule
+    assert res.iters == ref.iters and res.restarts == ref.restarts
+    np.testing.assert_allclose(beta.cpu().numpy(), ref.beta, rtol=1e-9, atol=1e-11)
+    assert res.primal_loop == pytest.approx(ref.primal, rel=1e-10)
+    assert res.dual_loop == pytest.approx(ref.dual_bound, rel=1e-9, abs=1e-9)
 
 
 def test_watchdog_probe_times_out_and_the_context_survives(lib):

@@ -250,126 +250,138 @@ def test_prox_threshold_info():
     assert 0 <= n_top <= 10 <= n_nz
 
 
-# ----------------------------------------------------------------- losses
-@pytest.mark.parametrize("loss", ["ls", "logistic"])
-def test_loss_conjugate_fenchel_young(loss):
-    rng = np.random.default_rng(9)
-    n = 50
-    y = rng.standard_normal(n) if loss == "ls" else np.where(rng.random(n) < 0.5, -1.0, 1.0)
-    z = rng.standard_normal(n) * 2
-    zeta = -losses.grad_F(z, y, loss)
-    # equality F(z) + F*(-zeta) = -zeta'z at zeta = -grad F(z)
-    assert losses.F(z, y, loss) + losses.F_conj(-zeta, y, loss) == pytest.approx(
-        float(-zeta @ z), abs=1e-10 * n)
-    # inequality at other points
-    for _ in range(20):
-        z2 = rng.standard_normal(n) * 2
-        assert losses.F_conj(-zeta, y, loss) >= float(-zeta @ z2) - losses.F(z2, y, loss) - 1e-9
-    # gradient by central differences
-    e = np.zeros(n); e[3] = 1e-6
-    fd = (losses.F(z + e, y, loss) - losses.F(z - e, y, loss)) / 2e-6
-    assert losses.grad_F(z, y, loss)[3] == pytest.approx(fd, rel=1e-6)
+def _kkt_threshold(m, rho, kbar, M):
+    """The multiplier c >= 0 of the budget sum_Jf z_j <= kbar in the joint
+    problem min_{u,z} 1/2 ||u - v||^2 + rho/2 sum u_j^2 / z_j (Eq. 5 inside the
+    prox), found by bisection.  For fixed c each free coordinate decouples:
+    minimising over z_j gives an l1 weight c on u_j while z_j < 1, so
+    u_j = |v_j| - c and z_j = (|v_j| - c) / w(c) with w(c) = min(c / rho, M)
+    (the box |u_j| <= M z_j binds once c > rho M); z_j = 1 gives the J1 prox
+    min(|v_j| / (1 + rho), M).  sum_j z_j(c) falls in c; the root is c."""
+    if kbar <= 0:
+        return math.inf
+    if np.count_nonzero(m) <= kbar:
+        return 0.0
+
+    def zsum(c):
+        w = min(c / rho, M)
+        return float(np.sum(np.minimum(np.maximum(m - c, 0.0) / w, 1.0)))
+
+    # sum z(c) = kbar can hold on a whole interval (the box binds and the
+    # kbar-th and next |v_j| lie more than M apart): every c there is a
+    # multiplier and the prox is the same; take the interval's midpoint
+    lo, hi = 0.0, float(np.max(m))
+    for _ in range(200):                 # smallest root
+        mid = 0.5 * (lo + hi)
+        if zsum(mid) > kbar:
+            lo = mid
+        else:
+            hi = mid
+    c_lo = hi
+    lo, hi = c_lo, float(np.max(m))
+    for _ in range(200):                 # largest root
+        mid = 0.5 * (lo + hi)
+        if zsum(mid) >= kbar:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (c_lo + lo)
 
 
-def test_logistic_conjugate_scalar_sup():
-    # 1-D check of F*(w) = sup_z wz - log(1 + exp(-y z)) by a dense grid
-    zs = np.linspace(-40, 40, 400001)
-    for y in (-1.0, 1.0):
-        for u in (0.1, 0.5, 0.93):
-            w = -y * u
-            sup = np.max(w * zs - np.logaddexp(0, -y * zs))
-            assert losses.F_conj(np.array([w]), np.array([y]), "logistic") == pytest.approx(sup, abs=1e-6)
+def _threshold_cases():
+    """Tie-free prox inputs with J0/J1 fixings, a slack budget, thresholds on
+    both sides of rho M (box inactive / active) and M = inf."""
+    rng = np.random.default_rng(21)
+    cases = []
+    for t in range(40):
+        p = int(rng.integers(30, 400))
+        k = int(rng.integers(1, 12))
+        n1 = int(rng.integers(0, min(k, 4) + 1))
+        n0 = int(rng.integers(0, p // 5))
+        fix = rand_fix(rng, p, n0, n1)
+        scale = [0.3, 1.0, 3.0, 10.0][t % 4]
+        v = rng.standard_normal(p) * scale
+        rho = float([0.02, 0.3, 1.0, 4.0][(t // 4) % 4])
+        M = [2.0, 0.5, math.inf, 1.0][(t // 16) % 4] if t % 7 else 0.2
+        cases.append((v, rho, fix, k, M))
+    # a slack budget: fewer nonzero free inputs than kbar
+    v = np.zeros(50)
+    v[[3, 17, 40]] = [1.5, -0.7, 2.5]
+    cases.append((v, 0.5, None, 5, 2.0))
+    return cases
 
 
-# ------------------------------------------------------------ whole solve
-def small_problem(loss, n=40, p=8, seed=0, rho=0.5):
-    X = synth.ar1_design(n, p, rho, seed)
-    s = synth.signal_from_design(X, 2)
-    y = synth.response(s, loss, 5.0, seed)
-    return X, y
+def test_prox_threshold_counts_from_independent_definitions():
+    """(n_top, n_nz) of prox_g against two definitions that share nothing with
+    its block scan of Algorithm 2: (i) read off the prox output alone, a free
+    coordinate is before the pooled block exactly when its output is the J1
+    prox min(|v_j| / (1 + rho), M) (pooled coordinates get |v_j| - c, which is
+    strictly smaller); (ii) from the KKT threshold c found by bisection,
+    n_top = #{|v_j| >= c + w(c)} and n_nz = #{|v_j| > c} over Jf."""
+    seen_box, seen_free, seen_slack = False, False, False
+    for v, rho, fix, k, M in _threshold_cases():
+        p = v.size
+        fixa = np.zeros(p, dtype=np.int8) if fix is None else fix
+        Jf = fixa == 0
+        kbar = k - int(np.sum(fixa > 0))
+        u, (n_top, n_nz) = R.prox_g(v, rho, fix, k, M, return_info=True)
+        m, uf = np.abs(v[Jf]), np.abs(u[Jf])
+        # (i) output classification
+        j1_like = np.minimum(m / (1.0 + rho), M)
+        top_i = (uf > 0) & np.isclose(uf, j1_like, rtol=1e-12, atol=0.0)
+        assert n_nz == int(np.count_nonzero(uf))
+        assert n_top == int(np.count_nonzero(top_i)), (n_top, int(np.count_nonzero(top_i)))
+        # (ii) KKT threshold
+        c = _kkt_threshold(m, rho, kbar, M)
+        if math.isinf(c):
+            assert n_top == n_nz == 0
+            continue
+        if c == 0.0:
+            seen_slack = True
+            assert n_top == n_nz == int(np.count_nonzero(m))
+            continue
+        w = min(c / rho, M)
+        T = c + w
+        # tie-free: no free input sits within 1e-9 of a breakpoint
+        assert np.all(np.abs(m - T) > 1e-9 * T) and np.all(np.abs(m - c) > 1e-9 * c)
+        assert n_top == int(np.count_nonzero(m >= T))
+        assert n_nz == int(np.count_nonzero(m > c))
+        # the pooled coordinates' outputs are |v_j| - c (Algorithm 2's block value)
+        mid = (m > c) & (m < T)
+        np.testing.assert_allclose(uf[mid], m[mid] - c, rtol=1e-9, atol=1e-12)
+        seen_box |= c > rho * M
+        seen_free |= c < rho * M
+    assert seen_box and seen_free and seen_slack
 
 
-def test_ridge_closed_form_k_equals_p():
-    X, y = small_problem("ls", n=60, p=10)
-    lam2 = 0.7
-    res = solver.solve(X, y, "ls", k=10, lambda2=lam2, M=math.inf, gap_tol=1e-12,
-                       max_iters=20000)
-    b = brute.ridge(X, y, lam2)
-    # |beta - beta*| ~ sqrt(gap / lambda2): the objective pins below are the tight ones
-    np.testing.assert_allclose(res.beta, b, rtol=1e-4, atol=1e-6)
-    opt = float(np.sum((y - X @ b) ** 2) + lam2 * b @ b)
-    assert res.dual_bound == pytest.approx(opt, rel=1e-10)
-    assert res.primal == pytest.approx(opt, rel=1e-10)
+def test_prox_threshold_counts_catch_block_scan_mistakes():
+    """The pin above is sensitive to the plausible mistakes of a block scan:
+    counting the pooled block's end instead of its start, a start off by one,
+    or the block that holds sorted position kbar (0-based) instead of the one
+    straddling kbar - 1 and kbar.  Each mutant disagrees with the KKT count on
+    some of the same inputs."""
+    mutants = {"end": 0, "start-1": 0, "start+1": 0, "pos-kbar": 0}
+    for v, rho, fix, k, M in _threshold_cases():
+        p = v.size
+        fixa = np.zeros(p, dtype=np.int8) if fix is None else fix
+        kbar = k - int(np.sum(fixa > 0))
+        Jf = fixa == 0
+        m = np.abs(v[Jf])
+        c = _kkt_threshold(m, rho, kbar, M)
+        if not (0.0 < c < math.inf):
+            continue
+        truth = int(np.count_nonzero(m >= c + min(c / rho, M)))
+        _, (n_top, n_nz) = R.prox_g(v, rho, fix, k, M, return_info=True)
+        assert n_top == truth
+        _, blocks = R.prox_gstar(v / rho, 1.0 / rho, fix, k, M, return_blocks=True)
 
-
-@pytest.mark.parametrize("loss", ["ls", "logistic"])
-def test_relaxation_below_bruteforce(loss):
-    rng = np.random.default_rng(10)
-    for trial in range(4):
-        p = 8
-        X, y = small_problem(loss, n=30, p=p, seed=trial)
-        fix = rand_fix(rng, p, int(rng.integers(0, 2)), int(rng.integers(0, 2)))
-        k = int(np.sum(fix > 0)) + 2
-        lam2, M = 0.5, 1.5
-        res = solver.solve(X, y, loss, k, lam2, M, fix=fix, gap_tol=1e-9, max_iters=50000)
-        assert res.converged
-        opt = brute.ksparse_opt(X, y, loss, k, lam2, M, fix)
-        assert res.dual_bound <= opt + 1e-9 * max(1, abs(opt))
-        assert res.primal <= opt + 1e-7 * max(1, abs(opt))
-
-
-@pytest.mark.parametrize("loss", ["ls", "logistic"])
-def test_relaxation_exact_without_cardinality(loss):
-    # k >= p: z = 1 is optimal, the relaxation IS problem (1) (perspective term exact)
-    X, y = small_problem(loss, n=30, p=6, seed=3)
-    lam2, M = 0.4, 1.2
-    res = solver.solve(X, y, loss, 6, lam2, M, gap_tol=1e-11, max_iters=50000)
-    opt, _ = brute.restricted_opt(X, y, loss, lam2, M, range(6))
-    assert res.dual_bound == pytest.approx(opt, rel=1e-7)
-
-
-def test_all_fixed_node_is_restricted_problem():
-    X, y = small_problem("ls", n=30, p=7, seed=4)
-    fix = np.array([1, -1, 1, -1, -1, 1, -1], dtype=np.int8)
-    lam2, M = 0.3, 1.0
-    res = solver.solve(X, y, "ls", 3, lam2, M, fix=fix, gap_tol=1e-11, max_iters=50000)
-    opt, _ = brute.restricted_opt(X, y, "ls", lam2, M, [0, 2, 5])
-    assert res.dual_bound == pytest.approx(opt, rel=1e-7)
-
-
-@pytest.mark.parametrize("loss", ["ls", "logistic"])
-def test_weak_duality_and_restart_contraction(loss):
-    X, y = small_problem(loss, n=80, p=40, seed=5, rho=0.7)
-    res = solver.solve(X, y, loss, 4, 0.3, 2.0, gap_tol=1e-9, record=True, max_iters=20000)
-    assert res.converged
-    phis = [h[1] for h in res.history]
-    psis = [h[2] for h in res.history]
-    assert max(psis) <= min(phis) + 1e-10 * max(1, abs(min(phis)))
-    # every restart happens only after the gap has contracted by eta
-    eta = math.e ** 3
-    ref = phis[0] - psis[0]
-    for (t, phi, psi, rs) in res.history[1:]:
-        if rs:
-            assert phi - psi <= ref / eta * (1 + 1e-12)
-            ref = phi - psi
-    assert res.restarts >= 2
-
-
-def test_restart_beats_plain_fista():
-    X, y = small_problem("ls", n=120, p=60, seed=6, rho=0.8)
-    L = solver.lipschitz(X, "ls")
-    a = solver.solve(X, y, "ls", 5, 0.05, 2.0, gap_tol=1e-10, L=L, max_iters=4000)
-    b = solver.solve(X, y, "ls", 5, 0.05, 2.0, gap_tol=1e-10, L=L, max_iters=4000,
-                     eta=math.inf)
-    assert a.converged
-    assert a.iters < b.iters or not b.converged
-
-
-def test_spectral_norm_power_iteration_matches_svd():
-    X = synth.ar1_design(300, 400, 0.6, 1)
-    want = float(np.linalg.norm(X, 2) ** 2)
-    # force the power-iteration branch
-    Xb = np.tile(X, (12, 10))
-    got = solver.spectral_norm_sq(Xb, iters=2000)
-    assert got == pytest.approx(float(np.linalg.norm(Xb, 2) ** 2), rel=1e-8)
-    assert want > 0
+        def scan(pick, pos_lo, pos_hi):
+            for s_, e_ in blocks:
+                if s_ <= pos_lo <= e_ and e_ >= pos_hi:
+                    return max(0, min(pick(s_, e_), n_nz))
+            return n_nz
+        mutants["end"] += scan(lambda s_, e_: e_ + 1, kbar - 1, kbar) != truth
+        mutants["start-1"] += scan(lambda s_, e_: s_ - 1, kbar - 1, kbar) != truth
+        mutants["start+1"] += scan(lambda s_, e_: s_ + 1, kbar - 1, kbar) != truth
+        mutants["pos-kbar"] += scan(lambda s_, e_: s_, kbar, kbar + 1) != truth
+    assert all(v > 0 for v in mutants.values()), mutants

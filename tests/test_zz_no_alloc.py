@@ -1,5 +1,6 @@
 """prox_persp_noalloc (scratch in the library's fixed device array) against
-prox_persp (stream-ordered scratch), through the C ABI, on two calls in a row.
+the FP64 oracle's prox (Algorithm 2 + Eq. prox:gN) and against prox_persp
+(stream-ordered scratch), through the C ABI, on two calls in a row.
 
 Same tolerances as the prox parity tests: FP64 outputs to 1e-12 relative, FP32
 to 2^-22 relative, threshold counts (n_top, n_nz) equal.  Collected last so
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import regularizer as R
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -60,6 +62,28 @@ def test_noalloc_matches_prox_persp_twice(lib, case, dtype):
         torch.cuda.synchronize()
         _close(out.double().cpu().numpy(), ref.double().cpu().numpy(), dtype)
         assert c_out.cpu().tolist() == c_ref.cpu().tolist()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("case", CASES)
+def test_noalloc_matches_oracle_twice(lib, case, dtype):
+    p, k, rho, M, n0, n1 = case
+    lam2 = 0.5
+    step = rho / (2 * lam2)
+    fix = _fix(p, n0, n1, p + k)
+    fix_h = None if fix is None else fix.cpu().numpy()
+    for call, scale in enumerate((2.0, 0.4)):
+        v = synth.prox_input(p, seed=5 * p + call, scale=scale)
+        if dtype == torch.float32:
+            v = v.astype(np.float32).astype(np.float64)   # the oracle sees the values the device sees
+        want, (ntop, nnz) = R.prox_g(v, rho, fix_h, k, M, return_info=True)
+        vd = torch.tensor(v, dtype=dtype, device="cuda")
+        out = torch.full_like(vd, float("nan"))
+        c_out = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+        lib.prox_persp_noalloc(vd, out, step, k, lam2, M, fix, c_out)
+        torch.cuda.synchronize()
+        _close(out.double().cpu().numpy(), want, dtype)
+        assert c_out.cpu().tolist() == [ntop, nnz]
 
 
 def test_noalloc_rejects_p_beyond_its_scratch(lib):
