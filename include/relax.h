@@ -153,14 +153,18 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
  *   warm_start: device [nb][p] of the handle's dtype, or NULL (zero).
  *   beta_out: device [nb][p] of the handle's dtype: each node's best primal point.
  *   out: host relax_result[nb], filled per node.
- * Per iteration the active nodes' points are the columns of a matrix B;
- * Z = X B and G = X' R run as two GEMMs (FP32 X: FP32 emulated on the BF16
- * tensor cores from 32 active nodes on, plain FP32 below; FP64 X: FP64), and
- * each node's prox / g / g* / gap / restart step runs in its own segment of
- * one launch.  Nodes converge after uneven iteration counts and leave the
- * batch every 16 iterations; the stall rule's window is at most 200 inside a
- * batch, and a node that stalls above gap_tol is finished by relax_solve's
- * loop from its best point (out[j].polish_iters).  Each node's bound is
+ * Per iteration the active nodes' points are the rows of a matrix B;
+ * Z = X B' and G = X' R run as two products (FP32 X: the library's
+ * tensor-core kernel on BF16 planes of X, X', B and R, FP32-accurate products
+ * summed over K chunks in FP64; FP64 X: FP64 products), and each node's
+ * prox / g / g* / gap / restart step runs in its own segment of one launch.
+ * Nodes converge after uneven iteration counts and leave the batch every 16
+ * iterations (each round of 16 is one CUDA graph per active-set size); the
+ * stall rule's window is at most 200 inside a batch, and a node that stalls
+ * above gap_tol is finished by relax_solve's loop from its best point
+ * (out[j].polish_iters).  The first batched call of a FP32 handle builds the
+ * BF16 planes of X and X' (six bytes per element of X each) and times a few
+ * K-chunk choices per product, keeping the fastest for the handle.  Each node's bound is
  * certified in FP64 as in relax_solve (without resuming).  Needs FP32 or
  * FP64 storage of X (RELAX_ENOTSUP for BF16/FP8).  Returns RELAX_OK when every
  * node certified gap_tol, else the first failing node's status (out[j].status
@@ -168,6 +172,19 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
 relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixings,
                                const void* warm_start, double gap_tol, void* beta_out,
                                relax_result* out);
+
+/* The two products of a batched iteration on their own, with the identity
+ * link: for nb points b_s (the rows of `points`), z_s = X b_s and
+ * g_s = X' z_s, i.e. the operator X'X of the power iteration, through exactly
+ * the kernels relax_solve_batch uses (the matrix-vector products that
+ * dominate the method, Sec. 5.2; stacked as matrix products for many nodes).
+ *   points: device [nb][p] of the handle's dtype.
+ *   z_out: device double [nb][n]; g_out: device double [nb][p].
+ * FP32 X: tensor-core products on BF16 planes (FP32-accurate products, FP64
+ * sums of the K chunks); FP64 X: FP64 products.  Needs FP32 or FP64 storage
+ * (RELAX_ENOTSUP otherwise).  Synchronizes the handle's stream. */
+relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const void* points, double* z_out,
+                               double* g_out);
 
 /* Dynamic termination of Sec. 5.3 for the handle's later solves (single and
  * batched): with cutoff = f(X b) + lambda2 ||b||^2 of the incumbent b, a

@@ -15,7 +15,8 @@ RELAX_F64, RELAX_F32, RELAX_BF16, RELAX_FP8E4M3 = 0, 1, 2, 3
 STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA", 4: "RELAX_ENOTCONV",
           5: "RELAX_ETIMEOUT", 6: "RELAX_ENUMERIC", 7: "RELAX_EINVALID_BOUND", 8: "RELAX_ENOTSUP"}
 
-EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_set_cutoff", "relax_xpass", "relax_certify",
+EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_set_cutoff", "relax_xpass", "relax_batch_xpass",
+           "relax_certify",
            "relax_destroy", "relax_watchdog_probe",
            "prox_persp", "prox_persp_noalloc", "gval_persp", "gstar_persp",
            "relax_mlp_features", "relax_mlp_forward", "relax_mlp_grad", "relax_mlp_adam",
@@ -75,6 +76,7 @@ def load():
                                  ctypes.POINTER(Options), vp]
     lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
     lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_batch_xpass.argtypes = [vp, i32, vp, vp, vp]
     lib.relax_set_cutoff.argtypes = [vp, dbl]
     lib.relax_watchdog_probe.argtypes = [i32, ctypes.POINTER(dbl), vp]
     lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
@@ -345,6 +347,17 @@ class Handle:
         g = torch.empty(self.p, dtype=self.dtype, device=self.X.device)
         loss = relax_xpass(self.h, beta, z, g)
         return z, g, loss
+
+    def batch_xpass(self, points):
+        """relax_batch_xpass: (z, g) = (X b_s, X' X b_s) for the rows b_s of
+        `points` (nb x p, the handle's dtype), as FP64 device tensors."""
+        import torch
+        nb = points.shape[0]
+        self._vec(points, "points", rows=nb)
+        z = torch.empty((nb, self.n), dtype=torch.float64, device=self.X.device)
+        g = torch.empty((nb, self.p), dtype=torch.float64, device=self.X.device)
+        _check(load().relax_batch_xpass(self.h, int(nb), _ptr(points), _ptr(z), _ptr(g)), "relax_batch_xpass")
+        return z, g
 
     def set_cutoff(self, cutoff=float("inf")):
         """Dynamic termination against the incumbent's objective (inf: off)."""

@@ -61,7 +61,7 @@ class BnBStats:
     cut_prune: int = 0           # children stopped by rule 2 (Psi >= incumbent)
     seconds: float = 0.0
     pairs: list = field(default_factory=list)   # (parent beta, child fix, child beta) when recording
-    bounds: list = field(default_factory=list)  # (parent bound, child bound) of every child solved
+    bounds: list = field(default_factory=list)  # (parent bound, child's certified bound, cutoff rule) per child
 
 
 def _branch_var(beta, fix):
@@ -170,14 +170,17 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
                 break
             start = learned(node.beta, f) if warm == "learned" else node.beta
             beta, res, code = solve(f, start)
-            st.bounds.append((node.bound, res.dual_bound))
+            st.bounds.append((node.bound, res.dual_bound, res.cutoff_rule))
             if record:
                 st.pairs.append((node.beta.clone(), f.copy(), beta.clone()))
             if code not in (0, 4):
                 st.dropped.append(node.bound)      # a failed solve proves nothing about the child
                 continue
-            if res.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
-                heapq.heappush(heap, Node(res.dual_bound, seq, f, beta, res.iters))
+            # the parent's bound holds for the child too (its feasible set is a
+            # subset); a child stopped early by rule 1 may have certified less
+            bound = max(res.dual_bound, node.bound)
+            if bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
+                heapq.heappush(heap, Node(bound, seq, f, beta, res.iters))
                 seq += 1
                 try_incumbent(beta.double().cpu().numpy(), f)
     h.set_cutoff(float("inf"))
@@ -231,14 +234,15 @@ def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, he
             st.iters += r.iters + r.polish_iters
             count_cut(r)
             b = betas[i].clone()
-            st.bounds.append((p.bound, r.dual_bound))
+            st.bounds.append((p.bound, r.dual_bound, r.cutoff_rule))
             if record:
                 st.pairs.append((p.beta.clone(), f.copy(), b))
             if r.status not in (0, 4):
                 st.dropped.append(p.bound)
                 continue
-            if r.dual_bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
-                heapq.heappush(heap, Node(r.dual_bound, seq, f, b, r.iters))
+            bound = max(r.dual_bound, p.bound)
+            if bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
+                heapq.heappush(heap, Node(bound, seq, f, b, r.iters))
                 seq += 1
                 try_incumbent(b.double().cpu().numpy(), f)
 

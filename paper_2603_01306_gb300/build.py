@@ -75,7 +75,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> dict:
         objs = [f.result() for f in futs]
         fsyn.result()
     lib = os.path.join(libdir, "librelax.so")
-    _link(sorted(objs), lib, ("-lcublas",))   # batched solves: X B and X' R products
+    _link(sorted(objs), lib)
     slib = os.path.join(synth_dir, "libsynth.so")
     _link([synth_obj], slib)
     if verbose:

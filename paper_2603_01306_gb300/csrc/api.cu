@@ -1,6 +1,5 @@
 // C ABI of the library (include/relax.h): handle lifecycle, the solve loop,
 // FP64 certification and the standalone regularizer entry points.
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -12,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "bgemm.cuh"
 #include "launch.cuh"
 #include "relax.h"
 #include "warmstart.h"
@@ -205,7 +205,15 @@ inline unsigned grid_for(int64_t work, int block = 256) {
 
 // ================================================================== handle
 struct relax_handle {
-  cublasHandle_t cublas = nullptr;   // batched solves: X B and X' R products (created on first use)
+  // batched solves of FP32 data: BF16 planes of X (K = p) and of X' (K = n)
+  // for the tensor-core products, built on the first batched call; the K
+  // chunks chosen per product and column tile width (BN / 16)
+  __nv_bfloat16* bx = nullptr;
+  __nv_bfloat16* bxt = nullptr;
+  int64_t ldbp = 0, ldbn = 0;
+  CUtensorMap tm_bx{}, tm_bxt{};
+  int bg_kc[2][BG_MAXN / 16 + 1] = {};
+  cudaEvent_t ev_t[2] = {nullptr, nullptr};   // timing of the chunk candidates
   int dev = 0;
   cudaStream_t stream = nullptr;
   int64_t n = 0, p = 0;
@@ -283,7 +291,9 @@ void handle_free(relax_handle* h) {
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_d) cudaFreeHost(h->h_d);
   if (h->h_i) cudaFreeHost(h->h_i);
-  if (h->cublas) cublasDestroy(h->cublas);
+  if (h->bx) cudaFree(h->bx);
+  if (h->bxt) cudaFree(h->bxt);
+  for (cudaEvent_t e : h->ev_t) if (e) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (cudaEvent_t e : h->ev) if (e) cudaEventDestroy(e);
   if (h->tev) {
@@ -797,6 +807,8 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRY(alloc((void**)&h->fixbuf, (size_t)p));
     TRYC(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
     TRYC(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+    TRYC(cudaEventCreate(&h->ev_t[0]));
+    TRYC(cudaEventCreate(&h->ev_t[1]));
     if (o.lipschitz > 0.0) h->L = o.lipschitz;
     else TRY(power_iteration(h, &h->L));
     TRYC(cudaStreamSynchronize(h->stream));
@@ -1255,34 +1267,97 @@ void set_error_detail(const char* msg) { snprintf(g_detail, sizeof(g_detail), "%
 
 // ======================================================= batched node solves
 // Many node relaxations of one design in lockstep: per iteration the active
-// nodes' points form the columns of B, Z = X B and G = X' R are two GEMMs
-// (FP32 data: FP32 emulated on the BF16 tensor cores from kEmulateMin columns
-// on, plain FP32 below; FP64: FP64), and the p-phase of every active node runs
-// in one segmented launch (one thread-block cluster per node, or cooperative
-// waves when p needs more CTAs than a cluster holds).  Converged nodes leave
-// the active set every kRetire iterations; a node stalled on the products'
-// floor is finished by the single-node loop.
+// nodes' points form the rows of B, and Z = X B' and G = X' R are two
+// products.  FP32 data: the library's tcgen05 kernel (bgemm.cu) on BF16
+// planes of X, X' and the operands (FP32-accurate products, FP64 sums of the
+// K chunks, fused with the link and the gradient layout).  FP64 data: plain
+// tiled FP64 products on the CUDA cores.  The p-phase of every active node
+// runs in one segmented launch (one thread-block cluster per node, or
+// cooperative waves when p needs more CTAs than a cluster holds).  Converged
+// nodes leave the active set every kRetire iterations; each round of kRetire
+// iterations is captured as a CUDA graph per active-set size; a node stalled
+// on the products' floor is finished by the single-node loop.
 namespace {
 
 constexpr int kRetire = 16;
-constexpr int kEmulateMin = 32;   // GEMM columns from which FP32 products use the tensor cores
 constexpr int kBatchStall = 200;  // least stall window inside a batch (iterations)
 
-// B[:, s] = the next point of node active[s], in the storage type of X
-template <typename TX>
-__global__ void batch_pack_kernel(const IterState* st, const int* active, int m, int64_t p, TX* Bm) {
+// FP64 data: B[s][j] = the next point of node active[s]
+__global__ void batch_pack_f64_kernel(const IterState* st, const int* active, int m, int64_t p, double* Bm) {
   const int s = blockIdx.y;
   if (s >= m) return;
   const double* b = static_cast<const double*>(st[active[s]].ps.beta);
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
-    Bm[(size_t)s * p + j] = (TX)b[j];
+    Bm[(size_t)s * p + j] = b[j];
 }
 
-// z of node active[s] to its state, and the link: R[:, s] = grad F(z) and,
-// for the logistic loop, R[:, m + s] = grad F at the momentum point
-template <typename TX>
-__global__ void batch_link_kernel(const IterState* st, const int* active, int m, int64_t n, const TX* Z,
-                                  const double* y, int loss, TX* R) {
+// FP64 products on the CUDA cores, 64 x 16 outputs per block of 256 threads
+// (4 per thread), K in steps of 32 through shared memory:
+//   Z[s][i] = sum_j X[i][j] B[s][j]        (rows i of X, points s)
+//   G[c][j] = sum_i X[i][j] R[c][i]        (columns j of X, right-hand sides c)
+__global__ void zprod_f64_kernel(const double* X, int64_t ldx, int64_t n, int64_t p, const double* B, int m,
+                                 double* Z) {
+  __shared__ double xs[64][33], bs[16][33];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int s0 = blockIdx.y * 16;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t k0 = 0; k0 < p; k0 += 32) {
+    for (int t = threadIdx.x; t < 64 * 32; t += 256) {
+      const int r = t >> 5, c = t & 31;
+      xs[r][c] = (i0 + r < n && k0 + c < p) ? X[(i0 + r) * ldx + k0 + c] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 16 * 32; t += 256) {
+      const int r = t >> 5, c = t & 31;
+      bs[r][c] = (s0 + r < m && k0 + c < p) ? B[(int64_t)(s0 + r) * p + k0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {
+      const double bv = bs[tx][c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += xs[ty + 16 * q][c] * bv;
+    }
+    __syncthreads();
+  }
+  if (s0 + tx < m)
+    for (int q = 0; q < 4; ++q)
+      if (i0 + ty + 16 * q < n) Z[(int64_t)(s0 + tx) * n + i0 + ty + 16 * q] = acc[q];
+}
+__global__ void gprod_f64_kernel(const double* X, int64_t ldx, int64_t n, int64_t p, const double* R, int nc,
+                                 double* G) {
+  __shared__ double xs[32][65], rs[16][33];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 16;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t k0 = 0; k0 < n; k0 += 32) {
+    for (int t = threadIdx.x; t < 32 * 64; t += 256) {
+      const int r = t >> 6, c = t & 63;
+      xs[r][c] = (k0 + r < n && j0 + c < p) ? X[(k0 + r) * ldx + j0 + c] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 16 * 32; t += 256) {
+      const int r = t >> 5, c = t & 31;
+      rs[r][c] = (c0 + r < nc && k0 + c < n) ? R[(int64_t)(c0 + r) * n + k0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const double rv = rs[tx][k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += xs[k][ty + 16 * q] * rv;
+    }
+    __syncthreads();
+  }
+  if (c0 + tx < nc)
+    for (int q = 0; q < 4; ++q)
+      if (j0 + ty + 16 * q < p) G[(int64_t)(c0 + tx) * p + j0 + ty + 16 * q] = acc[q];
+}
+
+// FP64 data: z of node active[s] to its state, and the link: R[s] = grad F(z)
+// and, for the logistic loop, R[m + s] = grad F at the momentum point
+__global__ void batch_link_f64_kernel(const IterState* st, const int* active, int m, int64_t n, const double* Z,
+                                      const double* y, int loss, double* R) {
   const int s = blockIdx.y;
   if (s >= m) return;
   const IterState& S = st[active[s]];
@@ -1291,27 +1366,26 @@ __global__ void batch_link_kernel(const IterState* st, const int* active, int m,
   const double* zprev = static_cast<const double*>(S.ps.zprev);
   const double mom = S.ps.mom;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double z = (double)Z[(size_t)s * n + i];
+    const double z = Z[(size_t)s * n + i];
     const double yd = y[i];
     zout[i] = z;
     if (loss == RELAX_LS) {
-      R[(size_t)s * n + i] = (TX)(2.0 * (z - yd));
+      R[(size_t)s * n + i] = 2.0 * (z - yd);
     } else {
-      R[(size_t)s * n + i] = (TX)(-yd / (1.0 + exp(yd * z)));
+      R[(size_t)s * n + i] = -yd / (1.0 + exp(yd * z));
       const double zy = (1.0 + mom) * z - mom * zprev[i];
-      R[(size_t)(m + s) * n + i] = (TX)(-yd / (1.0 + exp(yd * zy)));
+      R[(size_t)(m + s) * n + i] = -yd / (1.0 + exp(yd * zy));
     }
   }
 }
 
-// part[s][q][j] = G[j, q m + s] in FP64 (the p-phase's gradient layout)
-template <typename TX>
-__global__ void batch_grad_kernel(const TX* G, int m, int NB, int64_t p, double* part) {
+// FP64 data: part[s][q][j] = G[q m + s][j] (the p-phase's gradient layout)
+__global__ void batch_grad_f64_kernel(const double* G, int m, int NB, int64_t p, double* part) {
   const int s = blockIdx.y;
   if (s >= m) return;
   for (int q = 0; q < NB; ++q)
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x)
-      part[((size_t)s * NB + q) * p + j] = (double)G[(size_t)(q * m + s) * p + j];
+      part[((size_t)s * NB + q) * p + j] = G[(size_t)(q * m + s) * p + j];
 }
 
 __global__ void batch_done_kernel(const IterState* st, const int* active, int m, int* done) {
@@ -1319,10 +1393,75 @@ __global__ void batch_done_kernel(const IterState* st, const int* active, int m,
     done[s] = st[active[s]].done;
 }
 
-relax_status cublas_status(cublasStatus_t c) {
-  if (c == CUBLAS_STATUS_SUCCESS) return RELAX_OK;
-  snprintf(g_detail, sizeof(g_detail), "cuBLAS call failed: status %d", (int)c);
-  return c == CUBLAS_STATUS_ALLOC_FAILED ? RELAX_ENOMEM : RELAX_ECUDA;
+// BF16 planes of X and X' for the tensor-core products (built on the first
+// batched solve of a handle)
+relax_status ensure_planes(relax_handle* h) {
+  if (h->bx) return RELAX_OK;
+  const int64_t n = h->n, p = h->p;
+  h->ldbp = (p + 7) / 8 * 8;
+  h->ldbn = (n + 7) / 8 * 8;
+  relax_status rs = alloc((void**)&h->bx, sizeof(__nv_bfloat16) * 3 * (size_t)n * h->ldbp);
+  if (rs == RELAX_OK) rs = alloc((void**)&h->bxt, sizeof(__nv_bfloat16) * 3 * (size_t)p * h->ldbn);
+  if (rs != RELAX_OK) {
+    if (h->bx) cudaFree(h->bx);
+    h->bx = nullptr;
+    return rs;
+  }
+  CU(bgemm_split_x((const float*)h->X, n, p, h->ldx, false, h->bx, h->ldbp, h->stream));
+  CU(bgemm_split_x((const float*)h->X, n, p, h->ldx, true, h->bxt, h->ldbn, h->stream));
+  CU(bgemm_encode(&h->tm_bx, h->bx, p, n, h->ldbp, n, BG_BM));
+  CU(bgemm_encode(&h->tm_bxt, h->bxt, n, p, h->ldbn, p, BG_BM));
+  return RELAX_OK;
+}
+
+// The K chunks of one product of a batched solve: chosen once per handle,
+// product and column tile width by timing the candidates (about one to four
+// work units per SM) on the call's own operands, the fastest kept.
+relax_status tune_chunks(relax_handle* h, int which, BGArgs a, int M, int N, int K, BGPlan* best) {
+  BGPlan pl;
+  CU(bgemm_plan(pl, M, N, K, 0));
+  int& slot = h->bg_kc[which][pl.BN / 16];
+  if (slot > 0) {
+    CU(bgemm_plan(*best, M, N, K, slot));
+    return RELAX_OK;
+  }
+  int nsm = 0;
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  const int tiles = pl.MT * pl.NT;
+  cudaEvent_t e0 = h->ev_t[0], e1 = h->ev_t[1];
+  float best_ms = INFINITY;
+  int best_kc = pl.KC, last_kc = -1;
+  for (int w = 1; w <= 4; ++w) {
+    BGPlan c;
+    CU(bgemm_plan(c, M, N, K, (w * nsm + tiles - 1) / tiles));
+    if (c.KC == last_kc) continue;
+    last_kc = c.KC;
+    a.BN = c.BN; a.NT = c.NT; a.MT = c.MT; a.KC = c.KC; a.kc_blocks = c.kc_blocks; a.nkb = c.nkb;
+    a.stages = c.stages;
+    CU(bgemm_launch(c, a, h->stream));   // warm-up
+    CU(cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < 2; ++r) CU(bgemm_launch(c, a, h->stream));
+    CU(cudaEventRecord(e1, h->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_kc = c.KC;
+    }
+  }
+  slot = best_kc;
+  CU(bgemm_plan(*best, M, N, K, best_kc));
+  return RELAX_OK;
+}
+
+void fill_bgargs(BGArgs& a, const BGPlan& pl, float* P, int* status, uint64_t limit_ns) {
+  a.M = pl.M; a.N = pl.N; a.K = pl.K;
+  a.BN = pl.BN; a.NT = pl.NT; a.MT = pl.MT; a.KC = pl.KC;
+  a.kc_blocks = pl.kc_blocks; a.nkb = pl.nkb; a.stages = pl.stages;
+  a.P = P;
+  a.status = status;
+  a.limit_ns = limit_ns;
 }
 
 }  // namespace
@@ -1377,14 +1516,18 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   unsigned long long* acc = nullptr;
   double* bpart = nullptr;
   unsigned long long* bars = nullptr;
-  void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;
+  void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;   // FP64 data: operands and products
+  __nv_bfloat16 *Bp = nullptr, *Rp = nullptr;                      // FP32 data: BF16 planes of B and R
+  float *P1 = nullptr, *P2 = nullptr;                               // FP32 data: partial products per K chunk
   double* part = nullptr;
   int* active_d = nullptr;
   int* done_d = nullptr;
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;             // one round of iterations per active-set size
   relax_status rs = RELAX_OK;
   auto cleanup = [&]() {
-    void* ptrs[] = {dst, vec, acc, bpart, bars, Bm, Zm, Rm, Gm, part, active_d, done_d};
+    void* ptrs[] = {dst, vec, acc, bpart, bars, Bm, Zm, Rm, Gm, Bp, Rp, P1, P2, part, active_d, done_d};
     for (void* q : ptrs) if (q) cudaFree(q);
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
   };
 #define BTRY(x)                    \
   do {                             \
@@ -1410,10 +1553,22 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   BTRY(alloc((void**)&acc, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)nb));
   BTRY(alloc((void**)&bpart, sizeof(double) * 2 * (size_t)segb * NBP * (size_t)nb));
   BTRY(alloc((void**)&bars, sizeof(unsigned long long) * (size_t)nb));
-  BTRY(alloc(&Bm, es * (size_t)p * nb));
-  BTRY(alloc(&Zm, es * (size_t)n * nb));
-  BTRY(alloc(&Rm, es * (size_t)n * NB * nb));
-  BTRY(alloc(&Gm, es * (size_t)p * NB * nb));
+  if (f64) {
+    BTRY(alloc(&Bm, es * (size_t)p * nb));
+    BTRY(alloc(&Zm, es * (size_t)n * nb));
+    BTRY(alloc(&Rm, es * (size_t)n * NB * nb));
+    BTRY(alloc(&Gm, es * (size_t)p * NB * nb));
+  } else {
+    BTRY(ensure_planes(h));
+    const size_t bpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbp;
+    const size_t rpb = sizeof(__nv_bfloat16) * 3 * (size_t)NB * nb * h->ldbn;
+    BTRY(alloc((void**)&Bp, bpb));
+    BTRY(alloc((void**)&Rp, rpb));
+    BTRY(alloc((void**)&P1, sizeof(float) * BG_MAXKC * (size_t)nb * n));
+    BTRY(alloc((void**)&P2, sizeof(float) * BG_MAXKC * (size_t)NB * nb * p));
+    BTRYC(cudaMemsetAsync(Bp, 0, bpb, h->stream));   // finite operands for the first timing runs
+    BTRYC(cudaMemsetAsync(Rp, 0, rpb, h->stream));
+  }
   BTRY(alloc((void**)&part, sizeof(double) * (size_t)p * NB * nb));
   BTRY(alloc((void**)&active_d, sizeof(int) * (size_t)nb));
   BTRY(alloc((void**)&done_d, sizeof(int) * (size_t)nb));
@@ -1457,26 +1612,6 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   }
   BTRYC(cudaGetLastError());
   BTRYC(cudaMemcpyAsync(dst, hs.data(), sizeof(IterState) * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
-  // ---- cuBLAS on the handle's stream
-  if (!h->cublas) {
-    cublasStatus_t c = cublasCreate(&h->cublas);
-    if (c != CUBLAS_STATUS_SUCCESS) { h->cublas = nullptr; BTRY(cublas_status(c)); }
-    cublasSetEmulationStrategy(h->cublas, CUBLAS_EMULATION_STRATEGY_EAGER);
-  }
-  BTRY(cublas_status(cublasSetStream(h->cublas, h->stream)));
-  // FP32 data: few columns make the products HBM-bound GEMVs, which plain FP32
-  // serves at the speed of reading X; from kEmulateMin columns on they are
-  // compute-bound and run as FP32 emulated on the BF16 tensor cores
-  const bool plain32 = std::getenv("RELAX_BATCH_FP32") != nullptr;   // FP32 on the FP32 pipes (comparison runs)
-  auto compute_type = [&](int cols) {
-    if (f64) return CUBLAS_COMPUTE_64F;
-    return (plain32 || cols < kEmulateMin) ? CUBLAS_COMPUTE_32F : CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
-  };
-  const cudaDataType_t dt = f64 ? CUDA_R_64F : CUDA_R_32F;
-  const double one64 = 1.0, zero64 = 0.0;
-  const float one32 = 1.0f, zero32 = 0.0f;
-  const void* one = f64 ? (const void*)&one64 : (const void*)&one32;
-  const void* zero = f64 ? (const void*)&zero64 : (const void*)&zero32;
   // ---- p-phase arguments (segmented)
   PArgs pa = base_pargs(h);
   pa.mode = PM_ITER;
@@ -1490,14 +1625,13 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   pa.bar = bars;
   pa.acc = acc;
   pa.bpart = bpart;
-  pa.tol = loop_tol;
   pa.fast_s1 = h->dtype == RELAX_F32 ? 1 : 0;
   pa.lossp = nullptr;
   pa.y = (const double*)h->y;
   pa.n = n;
   pa.seg_blocks = segb;
-  // a node on the floor of the GEMM products hands over to the single-node
-  // finish after a shorter stall than a single solve waits
+  // a node on the floor of the products hands over to the single-node finish
+  // after a shorter stall than a single solve waits
   if (pa.stall_min > kBatchStall) pa.stall_min = kBatchStall;
   // ---- the loop
   std::vector<int> active(nb), hdone(nb);
@@ -1507,42 +1641,112 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   for (int round = 0; round < max_rounds && !active.empty(); ++round) {
     const int m = (int)active.size();
     BTRYC(cudaMemcpyAsync(active_d, active.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, h->stream));
+    // products of this round's active-set size
+    BGPlan pl1, pl2;
+    BGArgs a1{}, a2{};
+    BatchIo io{};
+    if (!f64) {
+      BTRYC(bgemm_plan(pl1, (int)n, m, (int)p, 0));
+      BTRYC(bgemm_plan(pl2, (int)p, NB * m, (int)n, 0));
+      a1.tmA = h->tm_bx;
+      a2.tmA = h->tm_bxt;
+      BTRYC(bgemm_encode(&a1.tmB, Bp, p, m, h->ldbp, nb, pl1.BN));
+      BTRYC(bgemm_encode(&a2.tmB, Rp, n, (int64_t)NB * m, h->ldbn, (int64_t)NB * nb, pl2.BN));
+      fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
+      fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
+      BTRY(tune_chunks(h, 0, a1, (int)n, m, (int)p, &pl1));
+      BTRY(tune_chunks(h, 1, a2, (int)p, NB * m, (int)n, &pl2));
+      fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
+      fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
+      io.st = dst;
+      io.active = active_d;
+      io.m = m;
+      io.nb = nb;
+      io.n = n;
+      io.p = p;
+      io.ldp = h->ldbp;
+      io.ldn = h->ldbn;
+      io.NB = NB;
+      io.loss = h->loss;
+      io.y = (const double*)h->y;
+      io.Bp = Bp;
+      io.Rp = Rp;
+      io.P1 = P1;
+      io.KC1 = pl1.KC;
+      io.P2 = P2;
+      io.KC2 = pl2.KC;
+      io.part = part;
+    }
     const dim3 gp((unsigned)std::min<int64_t>(64, (p + 255) / 256), (unsigned)m);
     const dim3 gn((unsigned)std::min<int64_t>(64, (n + 255) / 256), (unsigned)m);
-    for (int it = 0; it < kRetire; ++it) {
-      if (f64) batch_pack_kernel<double><<<gp, 256, 0, h->stream>>>(dst, active_d, m, p, (double*)Bm);
-      else batch_pack_kernel<float><<<gp, 256, 0, h->stream>>>(dst, active_d, m, p, (float*)Bm);
-      // Z (n x m) = X (row-major n x ldx, i.e. column-major ldx x n) times B (p x m)
-      BTRY(cublas_status(cublasGemmEx(h->cublas, CUBLAS_OP_T, CUBLAS_OP_N, (int)n, m, (int)p, one, h->X, dt,
-                                      (int)h->ldx, Bm, dt, (int)p, zero, Zm, dt, (int)n, compute_type(m),
-                                      CUBLAS_GEMM_DEFAULT)));
-      if (f64) batch_link_kernel<double><<<gn, 256, 0, h->stream>>>(dst, active_d, m, n, (const double*)Zm, (const double*)h->y, h->loss, (double*)Rm);
-      else batch_link_kernel<float><<<gn, 256, 0, h->stream>>>(dst, active_d, m, n, (const float*)Zm, (const double*)h->y, h->loss, (float*)Rm);
-      // G (p x NB m) = X' R
-      BTRY(cublas_status(cublasGemmEx(h->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)p, NB * m, (int)n, one, h->X, dt,
-                                      (int)h->ldx, Rm, dt, (int)n, zero, Gm, dt, (int)p, compute_type(NB * m),
-                                      CUBLAS_GEMM_DEFAULT)));
-      if (f64) batch_grad_kernel<double><<<gp, 256, 0, h->stream>>>((const double*)Gm, m, NB, p, part);
-      else batch_grad_kernel<float><<<gp, 256, 0, h->stream>>>((const float*)Gm, m, NB, p, part);
-      BTRYC(cudaGetLastError());
-      if (clustered) {
-        PArgs pw = pa;
-        pw.seg_node = active_d;
-        pw.cluster = 1;
-        BTRYC(pphase_launch_clusters(pc, pw, m, h->stream));
-        ++launches;
-      } else {
-        for (int w0 = 0; w0 < m; w0 += wave) {
+    const dim3 gz((unsigned)((n + 63) / 64), (unsigned)((m + 15) / 16));
+    const dim3 gg((unsigned)((p + 63) / 64), (unsigned)((NB * m + 15) / 16));
+    int round_launches = 0;
+    auto enqueue_round = [&](cudaStream_t cs) -> cudaError_t {
+      round_launches = 0;
+      for (int it = 0; it < kRetire; ++it) {
+        cudaError_t e;
+        if (f64) {
+          batch_pack_f64_kernel<<<gp, 256, 0, cs>>>(dst, active_d, m, p, (double*)Bm);
+          zprod_f64_kernel<<<gz, 256, 0, cs>>>((const double*)h->X, h->ldx, n, p, (const double*)Bm, m, (double*)Zm);
+          batch_link_f64_kernel<<<gn, 256, 0, cs>>>(dst, active_d, m, n, (const double*)Zm, (const double*)h->y,
+                                                    h->loss, (double*)Rm);
+          gprod_f64_kernel<<<gg, 256, 0, cs>>>((const double*)h->X, h->ldx, n, p, (const double*)Rm, NB * m,
+                                               (double*)Gm);
+          batch_grad_f64_kernel<<<gp, 256, 0, cs>>>((const double*)Gm, m, NB, p, part);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        } else {
+          if ((e = batch_pack(io, cs)) != cudaSuccess) return e;
+          if ((e = bgemm_launch(pl1, a1, cs)) != cudaSuccess) return e;
+          if ((e = batch_reduce_link(io, cs)) != cudaSuccess) return e;
+          if ((e = bgemm_launch(pl2, a2, cs)) != cudaSuccess) return e;
+          if ((e = batch_reduce_grad(io, cs)) != cudaSuccess) return e;
+        }
+        round_launches += 5;
+        if (clustered) {
           PArgs pw = pa;
-          pw.seg_node = active_d + w0;
-          pw.part = part + (size_t)w0 * NB * p;
-          const int cnt = std::min(wave, m - w0);
-          BTRYC(pphase_launch_grid(pp, pw, cnt * segb, h->stream));
-          ++launches;
+          pw.seg_node = active_d;
+          pw.cluster = 1;
+          if ((e = pphase_launch_clusters(pc, pw, m, cs)) != cudaSuccess) return e;
+          ++round_launches;
+        } else {
+          for (int w0 = 0; w0 < m; w0 += wave) {
+            PArgs pw = pa;
+            pw.seg_node = active_d + w0;
+            pw.part = part + (size_t)w0 * NB * p;
+            const int cnt = std::min(wave, m - w0);
+            if ((e = pphase_launch_grid(pp, pw, cnt * segb, cs)) != cudaSuccess) return e;
+            ++round_launches;
+          }
         }
       }
-      launches += 5;
+      return cudaSuccess;
+    };
+    // one graph per active-set size, captured on its first round
+    cudaGraphExec_t gx = nullptr;
+    for (auto& g : graphs)
+      if (g.first == m) gx = g.second;
+    if (!gx) {
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cs = nullptr;
+      bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool lok = enqueue_round(cs) == cudaSuccess;
+        ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && lok && graph;
+        if (ok) ok = cudaGraphInstantiate(&gx, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+      }
+      if (cs) cudaStreamDestroy(cs);
+      if (ok) graphs.emplace_back(m, gx);
+      else { gx = nullptr; cudaGetLastError(); }
     }
+    if (gx) {
+      BTRYC(cudaGraphLaunch(gx, h->stream));
+    } else {
+      BTRYC(enqueue_round(h->stream));
+    }
+    launches += round_launches;
     batch_done_kernel<<<1, 256, 0, h->stream>>>(dst, active_d, m, done_d);
     BTRYC(cudaGetLastError());
     BTRYC(cudaMemcpyAsync(hdone.data(), done_d, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
@@ -1772,5 +1976,87 @@ extern "C" relax_status relax_mlp_features(relax_handle* h, const void* beta_par
   }
   cudaStreamSynchronize(h->stream);
   cudaFree(gbuf);
+  return rs;
+}
+
+// ================================================ batched products (diagnostic)
+extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const void* points, double* z_out,
+                                          double* g_out) {
+  if (!h || nb <= 0 || !points || !z_out || !g_out) return RELAX_EINVAL;
+  if (h->xk_loop != XK_F32 && h->xk_loop != XK_F64) return RELAX_ENOTSUP;
+  CU(cudaSetDevice(h->dev));
+  const int64_t n = h->n, p = h->p;
+  const dim3 gz((unsigned)((n + 63) / 64), (unsigned)((nb + 15) / 16));
+  const dim3 gg((unsigned)((p + 63) / 64), (unsigned)((nb + 15) / 16));
+  CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  if (h->xk_loop == XK_F64) {
+    zprod_f64_kernel<<<gz, 256, 0, h->stream>>>((const double*)h->X, h->ldx, n, p, (const double*)points, nb, z_out);
+    gprod_f64_kernel<<<gg, 256, 0, h->stream>>>((const double*)h->X, h->ldx, n, p, z_out, nb, g_out);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->stream));
+    return RELAX_OK;
+  }
+  relax_status rs = ensure_planes(h);
+  if (rs != RELAX_OK) return rs;
+  // scratch: the points in FP64, B and R planes, the partials of both products
+  const size_t b64 = sizeof(double) * (size_t)nb * p;
+  const size_t bpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbp;
+  const size_t rpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbn;
+  const size_t p1b = sizeof(float) * BG_MAXKC * (size_t)nb * n;
+  const size_t p2b = sizeof(float) * BG_MAXKC * (size_t)nb * p;
+  unsigned char* scr = nullptr;
+  rs = alloc((void**)&scr, b64 + bpb + rpb + p1b + p2b + 4 * 256);
+  if (rs != RELAX_OK) return rs;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  double* bsrc = reinterpret_cast<double*>(scr);
+  __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(scr + al(b64));
+  __nv_bfloat16* Rp = reinterpret_cast<__nv_bfloat16*>(scr + al(b64) + al(bpb));
+  float* P1 = reinterpret_cast<float*>(scr + al(b64) + al(bpb) + al(rpb));
+  float* P2 = reinterpret_cast<float*>(scr + al(b64) + al(bpb) + al(rpb) + al(p1b));
+  auto run = [&]() -> relax_status {
+    to_f64_kernel<<<grid_for((int64_t)nb * p), 256, 0, h->stream>>>(points, 0, bsrc, (int64_t)nb * p);
+    CU(cudaGetLastError());
+    BGPlan pl1, pl2;
+    CU(bgemm_plan(pl1, (int)n, nb, (int)p, 0));
+    CU(bgemm_plan(pl2, (int)p, nb, (int)n, 0));
+    BGArgs a1{}, a2{};
+    a1.tmA = h->tm_bx;
+    a2.tmA = h->tm_bxt;
+    CU(bgemm_encode(&a1.tmB, Bp, p, nb, h->ldbp, nb, pl1.BN));
+    CU(bgemm_encode(&a2.tmB, Rp, n, nb, h->ldbn, nb, pl2.BN));
+    fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
+    fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
+    BatchIo io{};
+    io.m = nb;
+    io.nb = nb;
+    io.n = n;
+    io.p = p;
+    io.ldp = h->ldbp;
+    io.ldn = h->ldbn;
+    io.NB = 1;
+    io.loss = -1;                 // identity link: the second product is X' z
+    io.bsrc = bsrc;
+    io.zdst = z_out;
+    io.Bp = Bp;
+    io.Rp = Rp;
+    io.P1 = P1;
+    io.KC1 = pl1.KC;
+    io.P2 = P2;
+    io.KC2 = pl2.KC;
+    io.part = g_out;              // NB = 1: part[s][0][j] = g_out[s * p + j]
+    CU(batch_pack(io, h->stream));
+    CU(bgemm_launch(pl1, a1, h->stream));
+    CU(batch_reduce_link(io, h->stream));
+    CU(bgemm_launch(pl2, a2, h->stream));
+    CU(batch_reduce_grad(io, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    int dst = 0;
+    CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dst != ST_OK) snprintf(g_detail, sizeof(g_detail), "batched products: device status %d", dst);
+    return map_dev_status(dst);
+  };
+  rs = run();
+  cudaStreamSynchronize(h->stream);
+  cudaFree(scr);
   return rs;
 }

@@ -1,0 +1,93 @@
+// Batched products of many node relaxations sharing X on the 5th-generation
+// tensor cores: D = A B^T with A (M x K) and B (N x K) both K-major, each
+// stored as three BF16 planes whose sum is the FP32 value exactly (8 + 8 + 8
+// significand bits).  Six BF16 products per element pair (the pairs of planes
+// whose significance sums to at most the third plane's) reproduce FP32
+// products to within 2^-23 relative, accumulated in FP32 in tensor memory.
+//
+// The K range is cut into chunks; each work unit (M-tile, N-tile, K-chunk)
+// writes its FP32 partial tile, and a reduction kernel sums the chunks in
+// FP64 in a fixed order (deterministic), fused with what consumes the
+// product: the link of the loss (Z = X B) or the per-node gradient layout of
+// the p-phase (G = X' R).
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "pphase.cuh"
+
+namespace relax {
+
+constexpr int BG_BM = 128;          // rows of A per tile (the MMA's M)
+constexpr int BG_SW = 64;           // bytes per tile row in shared memory (64-byte swizzle)
+constexpr int BG_BK = BG_SW / 2;    // K elements (BF16) per pipeline stage
+constexpr int BG_MAXN = 256;        // columns of D per tile (one MMA's N) at most
+constexpr int BG_PLANES = 3;
+constexpr int BG_MAXS = 8;          // pipeline stages at most
+constexpr int BG_THREADS = 192;     // producer warp, MMA warp, four epilogue warps
+constexpr int BG_MAXKC = 16;        // K chunks at most (partials are KC x N x M floats)
+
+struct BGArgs {
+  CUtensorMap tmA;        // planes of A: dims {K, M, 3}, box {BG_BK, 128, 3}
+  CUtensorMap tmB;        // planes of B: dims {K, N, 3}, box {BG_BK, BN, 3}
+  int M, N, K;
+  int BN, NT, MT, KC;     // tile columns, N-tiles, M-tiles, K-chunks
+  int kc_blocks, nkb;     // K blocks (of BG_BK) per chunk, K blocks over K
+  int stages;
+  float* P;               // [KC][N][M] FP32 partial products
+  int* status;
+  uint64_t limit_ns;
+};
+
+struct BGPlan {
+  int M = 0, N = 0, K = 0;
+  int BN = 16, NT = 1, MT = 1, KC = 1, kc_blocks = 1, nkb = 1, stages = 2, grid = 1;
+  size_t smem = 0;
+};
+
+// Tile plan of D (M x N) = A B^T over K: BN and the N-tiles from N, the
+// stages from shared memory, and KC chunks of K (kc <= 0: about three work
+// units per SM).
+cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K, int kc);
+// Tensor map of three BF16 planes [3][rows][ld] with `rows` rows of K valid
+// elements (ld >= K, a multiple of 8), box {BG_BK, box_rows, 3}, 64-byte swizzle.
+cudaError_t bgemm_encode(CUtensorMap* tm, const void* planes, int64_t K, int64_t rows, int64_t ld,
+                         int64_t plane_rows, int box_rows);
+cudaError_t bgemm_launch(const BGPlan& pl, const BGArgs& a, cudaStream_t st);
+// planes[3][rows][ld] of FP32 X (n x p, leading dimension ldx): rows = n,
+// K = p (transpose = false) or rows = p, K = n (transpose = true); padding
+// columns are zero.
+cudaError_t bgemm_split_x(const float* X, int64_t n, int64_t p, int64_t ldx, bool transpose, __nv_bfloat16* planes,
+                          int64_t ld, cudaStream_t st);
+
+// Per-iteration kernels of the batched solve around the two products.
+struct BatchIo {
+  const IterState* st;   // node states (NULL: the points are bsrc and z goes to zdst)
+  const int* active;     // active node of each column slot
+  int m;                 // active nodes
+  int nb;                // node slots allocated (plane row stride of B)
+  int64_t n, p;
+  int64_t ldp, ldn;      // plane leading dimensions (K = p, K = n)
+  int NB;                // right-hand sides per node (1 LS, 2 logistic)
+  int loss;              // RELAX_LS, RELAX_LOGISTIC, or -1: the identity link (R = Z)
+  const double* bsrc;    // st == NULL: the points, [m][p]
+  double* zdst;          // st == NULL: z of every point, [m][n]
+  const double* y;
+  __nv_bfloat16* Bp;     // [3][nb][ldp] planes of the node points
+  __nv_bfloat16* Rp;     // [3][NB nb][ldn] planes of the link (the second product's B)
+  const float* P1;       // [KC1][m][n] partials of Z = X B
+  int KC1;
+  const float* P2;       // [KC2][NB m][p] partials of G = X' R
+  int KC2;
+  double* part;          // [m][NB][p] gradients per node (p-phase layout)
+};
+// B planes of the active nodes' next points
+cudaError_t batch_pack(const BatchIo& io, cudaStream_t st);
+// z = sum of the Z partials (FP64): each node's z^t, and the planes of
+// grad F at z (and at the momentum point for the logistic loop)
+cudaError_t batch_reduce_link(const BatchIo& io, cudaStream_t st);
+// the gradients X' grad F of every node, summed over the chunks in FP64
+cudaError_t batch_reduce_grad(const BatchIo& io, cudaStream_t st);
+
+}  // namespace relax

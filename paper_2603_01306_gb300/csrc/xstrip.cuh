@@ -410,6 +410,10 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
             for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
         }
       }
+      // every read of the stage is done (the partials are in registers):
+      // hand it back to the producer before the butterfly
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyA[st]);
       // lane 2j: the strip partial of row j, as (hi, lo)
       TA mh[NF], ml[NF];
 #pragma unroll
@@ -427,8 +431,6 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           ml[f] = (TA)0;
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&emptyA[st]);   // stage free: the rest works on registers
       if (!have_scale) {
         // every CTA's max |beta_j| is in: the common scale of this pass
         if (!__all_sync(0xffffffffu, wait_count(a.zcnt, gridDim.x, a.limit_ns, a.status))) {

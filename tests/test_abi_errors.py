@@ -69,6 +69,11 @@ def test_solve_and_batch_reject_invalid_arguments():
     assert lib.relax_solve_batch(FAKE, 2, None, None, 0.0, FAKE, res_arr) == EINVAL
     assert lib.relax_solve_batch(FAKE, 2, None, None, 1e-6, None, res_arr) == EINVAL
     assert lib.relax_solve_batch(FAKE, 2, None, None, 1e-6, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(None, 2, FAKE, FAKE, FAKE) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 0, FAKE, FAKE, FAKE) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, None, FAKE, FAKE) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, FAKE, None, FAKE) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, FAKE, FAKE, None) == EINVAL
     assert lib.relax_set_cutoff(None, 1.0) == EINVAL
     assert lib.relax_set_cutoff(FAKE, math.nan) == EINVAL
     assert lib.relax_xpass(None, FAKE, None, FAKE, None) == EINVAL

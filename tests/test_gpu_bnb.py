@@ -16,6 +16,9 @@ torch = pytest.importorskip("torch")
 
 
 def test_sequential_and_batched_bnb(lib):
+    """With and without the dynamic termination of Sec. 5.3: children solved
+    to the gap have bounds at least their parent's; children stopped by
+    rule 1 carry an earlier (valid, looser) bound; rule 2 prunes."""
     from paper_2603_01306_gb300 import bnb
     w = synth.Workload("bb", 800, 2000, 0.8, 15, 0.2, "ls")
     X, y = synth.make_problem_cpu(w)
@@ -23,17 +26,26 @@ def test_sequential_and_batched_bnb(lib):
                    lambda2=w.lambda2, M=w.M)
     runs = {}
     for batch in (1, 16):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = bnb.run(h, w.k, max_nodes=97, gap_tol=1e-6, batch=batch)
-        torch.cuda.synchronize()
-        runs[batch] = (st, time.perf_counter() - t0)
+        for cutoff in (False, True):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = bnb.run(h, w.k, max_nodes=97, gap_tol=1e-6, batch=batch, cutoff=cutoff)
+            torch.cuda.synchronize()
+            runs[batch, cutoff] = (st, time.perf_counter() - t0)
     h.close()
-    for batch, (st, secs) in runs.items():
+    for (batch, cutoff), (st, secs) in runs.items():
         assert st.nodes == 97
         assert len(st.bounds) == st.nodes - 1                  # every child, not the root
-        for pb, cb in st.bounds:
-            assert cb >= pb - 2e-6 * max(1.0, abs(pb)), (batch, pb, cb)
+        for pb, cb, rule in st.bounds:
+            if rule == 0:
+                assert cb >= pb - 2e-6 * max(1.0, abs(pb)), (batch, pb, cb)
+            else:
+                assert cutoff
         assert st.best_bound <= st.incumbent * (1 + 2e-6)
-        print(f"batch {batch}: {st.nodes} nodes in {secs:.2f} s ({st.nodes / secs:.1f} nodes/s), "
-              f"iterations {st.iters}, incumbent {st.incumbent:.6f}, best open bound {st.best_bound:.6f}")
+        if not cutoff:
+            assert st.cut_branch == st.cut_prune == 0
+        print(f"batch {batch} cutoff {cutoff}: {st.nodes} nodes in {secs:.2f} s ({st.nodes / secs:.1f} nodes/s), "
+              f"iterations {st.iters} (rule 1: {st.cut_branch}, rule 2: {st.cut_prune}), "
+              f"incumbent {st.incumbent:.6f}, best open bound {st.best_bound:.6f}")
+    # the early stops save iterations
+    assert runs[1, True][0].cut_branch + runs[1, True][0].cut_prune > 0
