@@ -7,8 +7,8 @@ FISTA iteration, gap restarts, FP64 certification at the end), inputs resident
 in HBM.  X (4 GB) is larger than L2, so no flush is needed between steps.
 
 e2e: the same relaxation end to end through the public API from pinned host
-buffers: X and y copied to the device, handle created (Lipschitz constant by
-power iteration), solved, beta copied back, handle destroyed.
+buffers: X and y copied to the device, handle created (Lipschitz constant by a
+Lanczos estimate), solved, beta copied back, handle destroyed.
 
 Multi-GPU: one process per GPU (torchrun), each rank solves its own replica of
 the workload; no data-path collective (the path shards by independent node
@@ -325,7 +325,7 @@ def run_batch(device, workload=BATCH_WORKLOAD, reps=2, singles=16):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
-        if code != 0:
+        if code not in (0, 4):   # ENOTCONV: reported below as uncertified nodes
             raise RuntimeError(f"batch status {relax.STATUS[code]}")
     t = min(times[1:]) if reps > 1 else times[0]
     it = [r.iters for r in res]
@@ -340,14 +340,38 @@ def run_batch(device, workload=BATCH_WORKLOAD, reps=2, singles=16):
     torch.cuda.synchronize()
     ts = e0.elapsed_time(e1) * 1e-3
     agree = max(abs(a - b.dual_bound) / abs(a) for a, b in zip(single_bounds, res))
+    # the two products of a batched iteration alone (relax_batch_xpass on the
+    # nodes' solutions), timed with CUDA events around the tensor-core launches
+    betas, _, _ = h.solve_batch(nb, fixings=fixd, gap_tol=GAP_TOL)
+    h.batch_xpass(betas, timing=True)
+    ms = [h.batch_xpass(betas, timing=True)[2] for _ in range(5)]
+    z_ms = statistics.median(m[0] for m in ms)
+    g_ms = statistics.median(m[1] for m in ms)
+    mma_flops = 6 * 2 * w.n * w.p * nb          # six BF16 plane products per FP32 product
+    achieved = 2 * mma_flops / ((z_ms + g_ms) * 1e-3) / 1e12
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
     h.close()
-    return {"workload": workload, "nodes": nb, "value": nb / t, "unit": "node relaxations/s",
-            "seconds": t, "iters_min_med_max": [min(it), int(np.median(it)), max(it)],
+    certified = sum(1 for r in res if r.status == 0)
+    return {"workload": workload, "nodes": nb, "value": certified / t, "unit": "node relaxations/s",
+            "seconds": t, "nodes_certified": certified,
+            "iters_min_med_max": [min(it), int(np.median(it)), max(it)],
             "polished_nodes": sum(1 for r in res if r.polish_iters > 0),
             "max_certified_rel_gap": max(r.rel_gap for r in res),
             "single_node_fp32": {"value": singles / ts, "unit": "node relaxations/s", "nodes": singles},
             "max_rel_bound_diff_vs_single": agree,
-            "products": "cuBLAS GEMMs: FP32 emulated on the BF16 tensor cores from 32 active nodes, plain FP32 below"}
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "bgemm_kernel (Z = X B', G = X' R on tcgen05, BF16 planes)",
+                         "ms_per_product": [z_ms, g_ms],
+                         "fp32_equivalent_tflops": 2 * 2 * w.n * w.p * nb / ((z_ms + g_ms) * 1e-3) / 1e12,
+                         "flops_note": "achieved counts the BF16 MMA work (6 plane products x 2 n p nodes per "
+                                       "product); fp32_equivalent_tflops counts 2 n p nodes per product",
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst (of measured)" if peaks
+                         else "fallback 1900 TFLOP/s (of fallback)"},
+            "products": "the library's tcgen05 kernel on BF16 planes of X, X' and the node operands "
+                        "(FP32-accurate products, TMEM sums drained every 128 terms, FP64 sums of the K chunks); "
+                        "each round of 16 iterations is one CUDA graph"}
 
 
 def oracle_sample(Xh, yh, w, L, sample_iters):

@@ -81,7 +81,16 @@ typedef struct {
   int32_t stall_window; /* stall rule: the loop stops once its best duality gap has not
                           fallen by 10% over the last quarter of its iterations and over
                           at least this many; 0 -> 1000, < 0 -> off */
-  int32_t reserved[5];
+  /* The methods of the convergence study (Sec. 5.2).  Defaults: FISTA with
+   * the duality-gap restart of Sec. 3.4 and the fixed step 1/L. */
+  int32_t method;      /* 0 FISTA (Beck 2017 Sec. 10.7), 1 proximal gradient (Sec. 10.2) */
+  int32_t restart;     /* FISTA only: 0 duality gap (Sec. 3.4), 1 function value
+                          (restart when Phi rises, O'Donoghue and Candes), 2 none */
+  int32_t step_rule;   /* 0 fixed 1/L; 1 backtracking (Beck Sec. 10.4.2): from L/64, L
+                          doubles until F(X x) <= F(y) + <grad F(y), x - y> + L/2 ||x - y||^2
+                          (+ 1e-12 |F(y)| for rounding); each retry costs one more
+                          fused pass and p-phase, and L never decreases */
+  int32_t reserved[2];
 } relax_options;
 
 typedef struct {
@@ -105,6 +114,8 @@ typedef struct {
                           node stalled in the batch received (0: none) */
   int32_t cutoff_rule; /* dynamic termination (relax_set_cutoff): 0 none, 1 the loop's Phi
                           fell to the cutoff (branch), 2 its Psi reached it (prune) */
+  int32_t backtracks;  /* step_rule 1: rejected trial points (each doubled L); lipschitz
+                          is then the final L */
 } relax_result;
 
 /* Create a solver handle bound to one design X and response y (Sec. 2.3).
@@ -182,9 +193,12 @@ relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int8_t* fixing
  *   z_out: device double [nb][n]; g_out: device double [nb][p].
  * FP32 X: tensor-core products on BF16 planes (FP32-accurate products, FP64
  * sums of the K chunks); FP64 X: FP64 products.  Needs FP32 or FP64 storage
- * (RELAX_ENOTSUP otherwise).  Synchronizes the handle's stream. */
+ * (RELAX_ENOTSUP otherwise).
+ *   products_ms: host double[2] or NULL: FP32 X, the device time of the two
+ *      tensor-core launches (z, then g), from CUDA events on the handle's stream.
+ * Synchronizes the handle's stream. */
 relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const void* points, double* z_out,
-                               double* g_out);
+                               double* g_out, double* products_ms);
 
 /* Dynamic termination of Sec. 5.3 for the handle's later solves (single and
  * batched): with cutoff = f(X b) + lambda2 ||b||^2 of the incumbent b, a

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("watchdog_ms", ctypes.c_int32), ("no_certify", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("stall_window", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("stall_window", ctypes.c_int32), ("method", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("step_rule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Result(ctypes.Structure):
@@ -49,7 +50,7 @@ class Result(ctypes.Structure):
                 ("n_nz", ctypes.c_int32), ("launches", ctypes.c_int32), ("xpass_count", ctypes.c_int32),
                 ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double),
                 ("stalled", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("cutoff_rule", ctypes.c_int32)]
+                ("cutoff_rule", ctypes.c_int32), ("backtracks", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -76,7 +77,7 @@ def load():
                                  ctypes.POINTER(Options), vp]
     lib.relax_solve.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(Result)]
     lib.relax_xpass.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
-    lib.relax_batch_xpass.argtypes = [vp, i32, vp, vp, vp]
+    lib.relax_batch_xpass.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(dbl)]
     lib.relax_set_cutoff.argtypes = [vp, dbl]
     lib.relax_watchdog_probe.argtypes = [i32, ctypes.POINTER(dbl), vp]
     lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
@@ -144,8 +145,14 @@ def _need_cuda(*ts):
             raise ValueError("tensors must live on the GPU")
 
 
+METHODS = {"fista": 0, "pgd": 1}
+RESTARTS = {"gap": 0, "function": 1, "none": 2}
+STEP_RULES = {"fixed": 0, "backtracking": 1}
+
+
 def make_options(M=2.0, eta=0.0, lipschitz=0.0, max_iters=0, precision=0, watchdog_ms=0,
-                 certify=True, chunk=0, timing=False, stall_window=0) -> Options:
+                 certify=True, chunk=0, timing=False, stall_window=0, method="fista", restart="gap",
+                 step="fixed") -> Options:
     o = Options()
     o.M = float(M)
     o.eta = float(eta)
@@ -157,6 +164,9 @@ def make_options(M=2.0, eta=0.0, lipschitz=0.0, max_iters=0, precision=0, watchd
     o.chunk = int(chunk)
     o.timing = 1 if timing else 0
     o.stall_window = int(stall_window)
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
+    o.restart = RESTARTS[restart] if isinstance(restart, str) else int(restart)
+    o.step_rule = STEP_RULES[step] if isinstance(step, str) else int(step)
     return o
 
 
@@ -287,14 +297,15 @@ class Handle:
 
     def __init__(self, X, y, loss="ls", k=10, lambda2=1.0, M=2.0, eta=0.0, lipschitz=0.0,
                  max_iters=0, precision=0, certify=True, chunk=0, watchdog_ms=0, timing=False,
-                 stall_window=0):
+                 stall_window=0, method="fista", restart="gap", step="fixed"):
         self.loss = {"ls": RELAX_LS, "logistic": RELAX_LOGISTIC}[loss] if isinstance(loss, str) else loss
         self.X, self.y = X, y
         self.n, self.p = X.shape
         self.dtype = X.dtype
         self.opts = make_options(M=M, eta=eta, lipschitz=lipschitz, max_iters=max_iters,
                                  precision=precision, watchdog_ms=watchdog_ms, certify=certify,
-                                 chunk=chunk, timing=timing, stall_window=stall_window)
+                                 chunk=chunk, timing=timing, stall_window=stall_window, method=method,
+                                 restart=restart, step=step)
         self.h = relax_create(X, y, self.loss, k, lambda2, self.opts)
 
     def _vec(self, t, what, rows=None, dtype=None):
@@ -348,16 +359,19 @@ class Handle:
         loss = relax_xpass(self.h, beta, z, g)
         return z, g, loss
 
-    def batch_xpass(self, points):
+    def batch_xpass(self, points, timing=False):
         """relax_batch_xpass: (z, g) = (X b_s, X' X b_s) for the rows b_s of
-        `points` (nb x p, the handle's dtype), as FP64 device tensors."""
+        `points` (nb x p, the handle's dtype), as FP64 device tensors; with
+        timing also the device ms of the two tensor-core launches."""
         import torch
         nb = points.shape[0]
         self._vec(points, "points", rows=nb)
         z = torch.empty((nb, self.n), dtype=torch.float64, device=self.X.device)
         g = torch.empty((nb, self.p), dtype=torch.float64, device=self.X.device)
-        _check(load().relax_batch_xpass(self.h, int(nb), _ptr(points), _ptr(z), _ptr(g)), "relax_batch_xpass")
-        return z, g
+        ms = (ctypes.c_double * 2)()
+        _check(load().relax_batch_xpass(self.h, int(nb), _ptr(points), _ptr(z), _ptr(g), ms if timing else None),
+               "relax_batch_xpass")
+        return (z, g, (ms[0], ms[1])) if timing else (z, g)
 
     def set_cutoff(self, cutoff=float("inf")):
         """Dynamic termination against the incumbent's objective (inf: off)."""

@@ -213,7 +213,8 @@ struct relax_handle {
   int64_t ldbp = 0, ldbn = 0;
   CUtensorMap tm_bx{}, tm_bxt{};
   int bg_kc[2][BG_MAXN / 16 + 1] = {};
-  cudaEvent_t ev_t[2] = {nullptr, nullptr};   // timing of the chunk candidates
+  cudaEvent_t ev_t[2] = {nullptr, nullptr};   // timing of the chunk candidates and of the first product
+  cudaEvent_t ev_p[2] = {nullptr, nullptr};   // timing of the second product (relax_batch_xpass)
   int dev = 0;
   cudaStream_t stream = nullptr;
   int64_t n = 0, p = 0;
@@ -225,6 +226,7 @@ struct relax_handle {
   double M = 2.0, eta = 0.0;
   int max_iters = 100000, chunk = 32;
   int stall_min = 1000;      // least window of the stall rule (0: off)
+  int method = 0, restart_rule = 0, backtrack = 0;   // the convergence study's variants
   double cutoff = INFINITY;  // incumbent objective for the dynamic termination (inf: off)
   uint64_t limit_ns = 4000000000ull;
   bool certify = true;
@@ -250,8 +252,9 @@ struct relax_handle {
   double* colstat = nullptr;     // [2][p]: ||X_j||_2, |corr(X_j, y)| (learned warm start)
   IterState* st = nullptr;
   PassState* ps_aux = nullptr;
-  void* vb[13] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
-                             // z prev/cur (n); scratch p, p, n, n; z of the best dual (n)
+  void* vb[16] = {};         // FP64: beta prev/cur, G prev/cur, beta_best, beta_dbest (p);
+                             // z prev/cur (n); scratch p, p, n, n; z of the best dual (n);
+                             // backtracking: y and its gradient (p, p), X y (n)
   unsigned long long* acc = nullptr;
   double* bpart = nullptr;
   unsigned long long* bar = nullptr;
@@ -294,6 +297,7 @@ void handle_free(relax_handle* h) {
   if (h->bx) cudaFree(h->bx);
   if (h->bxt) cudaFree(h->bxt);
   for (cudaEvent_t e : h->ev_t) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_p) if (e) cudaEventDestroy(e);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (cudaEvent_t e : h->ev) if (e) cudaEventDestroy(e);
   if (h->tev) {
@@ -358,6 +362,9 @@ PArgs base_pargs(relax_handle* h) {
   a.eta = h->eta;
   a.max_iters = h->max_iters;
   a.stall_min = h->stall_min;
+  a.method = h->method;
+  a.restart_rule = h->restart_rule;
+  a.backtrack = h->backtrack;
   a.lossp = nullptr;
   a.acc = h->acc;
   a.bpart = h->bpart;
@@ -666,7 +673,8 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
   relax_options o{};
   if (opt) o = *opt;
   if (o.M < 0.0 || std::isnan(o.M) || o.eta < 0.0 || o.lipschitz < 0.0 || o.max_iters < 0 ||
-      o.watchdog_ms < 0 || o.chunk < 0)
+      o.watchdog_ms < 0 || o.chunk < 0 || o.method < 0 || o.method > 1 || o.restart < 0 || o.restart > 2 ||
+      o.step_rule < 0 || o.step_rule > 1)
     return RELAX_EINVAL;
   const int prec = o.precision == 0 ? dtype : o.precision;
   if (prec != dtype && !((prec == RELAX_BF16 || prec == RELAX_FP8E4M3) && dtype == RELAX_F32))
@@ -703,6 +711,9 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     h->max_iters = o.max_iters == 0 ? 100000 : o.max_iters;
     h->chunk = o.chunk == 0 ? 32 : o.chunk;
     h->stall_min = o.stall_window == 0 ? 1000 : std::max(0, o.stall_window);
+    h->method = o.method;
+    h->restart_rule = o.restart;
+    h->backtrack = o.step_rule;
     h->limit_ns = (uint64_t)(o.watchdog_ms == 0 ? 4000 : o.watchdog_ms) * 1000000ull;
     h->certify = o.no_certify == 0;
     const size_t es = h->esz();
@@ -770,7 +781,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       std::fprintf(stderr, "[relax] loop pass: xk=%d Gc=%d Gr=%d sw=%lld (%d x %d) B=%d nblk=%d SA=%d SB=%d lag=%d threads=%d smem=%zu\n",
                    q.xk, q.Gc, q.Gr, (long long)q.sw, q.nbox, q.inner, q.B, q.nblk, q.SA, q.SB, q.lag, q.threads, q.smem);
     }
-    TRYC(pphase_plan(h->pp_iter, true, p));
+    TRYC(pphase_plan(h->pp_iter, true, p, h->backtrack != 0));
     TRYC(pphase_plan(h->pp_eval, true, p));
     {
       const XSPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
@@ -790,6 +801,8 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     for (int i = 6; i < 8; ++i) TRY(alloc(&h->vb[i], (size_t)n * sizeof(double)));
     for (int i = 8; i < 10; ++i) TRY(alloc(&h->vb[i], (size_t)p * sizeof(double)));
     for (int i = 10; i < 13; ++i) TRY(alloc(&h->vb[i], (size_t)n * sizeof(double)));
+    for (int i = 13; i < 15; ++i) TRY(alloc(&h->vb[i], (size_t)p * sizeof(double)));
+    TRY(alloc(&h->vb[15], (size_t)n * sizeof(double)));
     TRY(alloc((void**)&h->acc, 3 * ACC_STRIDE * sizeof(unsigned long long)));
     const int gmax = std::max(h->pp_iter.grid, h->pp_eval.grid);
     TRY(alloc((void**)&h->bpart, (size_t)2 * gmax * NBP * sizeof(double)));
@@ -809,6 +822,8 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
     TRYC(cudaEventCreate(&h->ev_t[0]));
     TRYC(cudaEventCreate(&h->ev_t[1]));
+    TRYC(cudaEventCreate(&h->ev_p[0]));
+    TRYC(cudaEventCreate(&h->ev_p[1]));
     if (o.lipschitz > 0.0) h->L = o.lipschitz;
     else TRY(power_iteration(h, &h->L));
     TRYC(cudaStreamSynchronize(h->stream));
@@ -871,6 +886,11 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   s.ps.mom = 0.0;
   s.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
   s.cutoff = h->cutoff;
+  s.Lk = h->backtrack ? h->L / 64.0 : h->L;   // backtracking starts below the estimate and only grows
+  s.rho_last = 2.0 * h->lambda2 / s.Lk;
+  s.y_keep = h->vb[13];
+  s.gy_keep = h->vb[14];
+  s.zy_keep = h->vb[15];
   *h->h_state = s;
   CU(cudaMemcpyAsync(h->st, h->h_state, sizeof(IterState), cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
@@ -1048,6 +1068,8 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   }
   out->restarts = S.restarts;
   out->stalled = S.stalled;
+  out->backtracks = S.backtracks;
+  out->lipschitz = S.Lk;
   out->cutoff_rule = S.cut_rule;
   out->primal_loop = S.phi_best;
   out->dual_loop = S.psi_best;
@@ -1455,7 +1477,7 @@ relax_status tune_chunks(relax_handle* h, int which, BGArgs a, int M, int N, int
   return RELAX_OK;
 }
 
-void fill_bgargs(BGArgs& a, const BGPlan& pl, float* P, int* status, uint64_t limit_ns) {
+void fill_bgargs(BGArgs& a, const BGPlan& pl, double* P, int* status, uint64_t limit_ns) {
   a.M = pl.M; a.N = pl.N; a.K = pl.K;
   a.BN = pl.BN; a.NT = pl.NT; a.MT = pl.MT; a.KC = pl.KC;
   a.kc_blocks = pl.kc_blocks; a.nkb = pl.nkb; a.stages = pl.stages;
@@ -1503,14 +1525,14 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   // fewest CTAs that cover p in cooperative waves of co-resident segments
   PPlan pp = h->pp_iter;
   PPlan pc;
-  const bool clustered = pphase_cluster_plan(pc, p) == cudaSuccess && !std::getenv("RELAX_BATCH_WAVES");
+  const bool clustered = pphase_cluster_plan(pc, p, h->backtrack != 0) == cudaSuccess && !std::getenv("RELAX_BATCH_WAVES");
   cudaGetLastError();   // a refused cluster plan leaves no sticky error
   const int segb = clustered ? pc.seg
                              : (int)std::max<int64_t>(1, (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT));
   const int wave = std::max(1, pp.maxgrid / segb);
   if (!clustered && segb > pp.maxgrid) return RELAX_ENOTSUP;
   // ---- device memory of the batch
-  const size_t nvec = 6 * (size_t)p + 3 * (size_t)n;   // per node: 6 p-vectors, 3 n-vectors (FP64)
+  const size_t nvec = 8 * (size_t)p + 4 * (size_t)n;   // per node: 8 p-vectors, 4 n-vectors (FP64)
   IterState* dst = nullptr;
   double* vec = nullptr;
   unsigned long long* acc = nullptr;
@@ -1518,7 +1540,7 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   unsigned long long* bars = nullptr;
   void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;   // FP64 data: operands and products
   __nv_bfloat16 *Bp = nullptr, *Rp = nullptr;                      // FP32 data: BF16 planes of B and R
-  float *P1 = nullptr, *P2 = nullptr;                               // FP32 data: partial products per K chunk
+  double *P1 = nullptr, *P2 = nullptr;                              // FP32 data: partial products per K chunk
   double* part = nullptr;
   int* active_d = nullptr;
   int* done_d = nullptr;
@@ -1564,8 +1586,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     const size_t rpb = sizeof(__nv_bfloat16) * 3 * (size_t)NB * nb * h->ldbn;
     BTRY(alloc((void**)&Bp, bpb));
     BTRY(alloc((void**)&Rp, rpb));
-    BTRY(alloc((void**)&P1, sizeof(float) * BG_MAXKC * (size_t)nb * n));
-    BTRY(alloc((void**)&P2, sizeof(float) * BG_MAXKC * (size_t)NB * nb * p));
+    BTRY(alloc((void**)&P1, sizeof(double) * BG_MAXKC * (size_t)nb * n));
+    BTRY(alloc((void**)&P2, sizeof(double) * BG_MAXKC * (size_t)NB * nb * p));
     BTRYC(cudaMemsetAsync(Bp, 0, bpb, h->stream));   // finite operands for the first timing runs
     BTRYC(cudaMemsetAsync(Rp, 0, rpb, h->stream));
   }
@@ -1587,9 +1609,12 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     s.G_cur = v + 3 * p;
     s.beta_best = v + 4 * p;
     s.beta_dbest = v + 5 * p;
-    s.z_prev = v + 6 * p;
-    s.z_cur = v + 6 * p + n;
-    s.z_dbest = v + 6 * p + 2 * n;
+    s.y_keep = v + 6 * p;
+    s.gy_keep = v + 7 * p;
+    s.z_prev = v + 8 * p;
+    s.z_cur = v + 8 * p + n;
+    s.z_dbest = v + 8 * p + 2 * n;
+    s.zy_keep = v + 8 * p + 3 * n;
     s.tau = 1.0;
     s.gap_ref = INFINITY;
     s.phi_best = INFINITY;
@@ -1600,6 +1625,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     s.tol = loop_tol;
     s.cutoff_on = std::isfinite(h->cutoff) ? 1 : 0;
     s.cutoff = h->cutoff;
+    s.Lk = h->backtrack ? h->L / 64.0 : h->L;
+    s.rho_last = 2.0 * h->lambda2 / s.Lk;
     s.ps.beta = s.beta_cur;
     s.ps.zout = s.z_cur;
     s.ps.zprev = s.z_prev;
@@ -1811,6 +1838,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     o.lipschitz = h->L;
     o.iters = S.iter;
     o.restarts = S.restarts;
+    o.backtracks = S.backtracks;
+    o.lipschitz = S.Lk;
     o.primal_loop = S.phi_best;
     o.dual_loop = S.psi_best;
     o.launches = launches + (h->certify ? 4 * nb : 0);
@@ -1981,7 +2010,7 @@ extern "C" relax_status relax_mlp_features(relax_handle* h, const void* beta_par
 
 // ================================================ batched products (diagnostic)
 extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const void* points, double* z_out,
-                                          double* g_out) {
+                                          double* g_out, double* products_ms) {
   if (!h || nb <= 0 || !points || !z_out || !g_out) return RELAX_EINVAL;
   if (h->xk_loop != XK_F32 && h->xk_loop != XK_F64) return RELAX_ENOTSUP;
   CU(cudaSetDevice(h->dev));
@@ -2002,8 +2031,8 @@ extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const voi
   const size_t b64 = sizeof(double) * (size_t)nb * p;
   const size_t bpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbp;
   const size_t rpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbn;
-  const size_t p1b = sizeof(float) * BG_MAXKC * (size_t)nb * n;
-  const size_t p2b = sizeof(float) * BG_MAXKC * (size_t)nb * p;
+  const size_t p1b = sizeof(double) * BG_MAXKC * (size_t)nb * n;
+  const size_t p2b = sizeof(double) * BG_MAXKC * (size_t)nb * p;
   unsigned char* scr = nullptr;
   rs = alloc((void**)&scr, b64 + bpb + rpb + p1b + p2b + 4 * 256);
   if (rs != RELAX_OK) return rs;
@@ -2011,8 +2040,8 @@ extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const voi
   double* bsrc = reinterpret_cast<double*>(scr);
   __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(scr + al(b64));
   __nv_bfloat16* Rp = reinterpret_cast<__nv_bfloat16*>(scr + al(b64) + al(bpb));
-  float* P1 = reinterpret_cast<float*>(scr + al(b64) + al(bpb) + al(rpb));
-  float* P2 = reinterpret_cast<float*>(scr + al(b64) + al(bpb) + al(rpb) + al(p1b));
+  double* P1 = reinterpret_cast<double*>(scr + al(b64) + al(bpb) + al(rpb));
+  double* P2 = reinterpret_cast<double*>(scr + al(b64) + al(bpb) + al(rpb) + al(p1b));
   auto run = [&]() -> relax_status {
     to_f64_kernel<<<grid_for((int64_t)nb * p), 256, 0, h->stream>>>(points, 0, bsrc, (int64_t)nb * p);
     CU(cudaGetLastError());
@@ -2045,11 +2074,22 @@ extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const voi
     io.KC2 = pl2.KC;
     io.part = g_out;              // NB = 1: part[s][0][j] = g_out[s * p + j]
     CU(batch_pack(io, h->stream));
+    CU(cudaEventRecord(h->ev_t[0], h->stream));
     CU(bgemm_launch(pl1, a1, h->stream));
+    CU(cudaEventRecord(h->ev_t[1], h->stream));
     CU(batch_reduce_link(io, h->stream));
+    CU(cudaEventRecord(h->ev_p[0], h->stream));
     CU(bgemm_launch(pl2, a2, h->stream));
+    CU(cudaEventRecord(h->ev_p[1], h->stream));
     CU(batch_reduce_grad(io, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    if (products_ms) {
+      float t1 = 0.f, t2 = 0.f;
+      CU(cudaEventElapsedTime(&t1, h->ev_t[0], h->ev_t[1]));
+      CU(cudaEventElapsedTime(&t2, h->ev_p[0], h->ev_p[1]));
+      products_ms[0] = t1;
+      products_ms[1] = t2;
+    }
     int dst = 0;
     CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (dst != ST_OK) snprintf(g_detail, sizeof(g_detail), "batched products: device status %d", dst);

@@ -24,16 +24,19 @@ __host__ __device__ inline uint32_t bg_stage_bytes(int BN) {
 }
 
 // Persistent: CTA c takes work units c, c + grid, ... in order.  A unit is
-// (M-tile, N-tile, K-chunk); its tile of D accumulates in one of two TMEM
-// buffers while the epilogue drains the other.
+// (M-tile, N-tile, K-chunk).  Its K blocks are taken BG_DRAIN at a time (a
+// period): the MMAs of a period accumulate in one of BG_NBUF TMEM buffer
+// pairs (main product, corrections), which the epilogue then adds into the
+// unit's FP32 sums in registers while the MMAs fill the next pair.
 //   warp 0 lane 0: TMA producer (A and B planes of one K block per stage)
 //   warp 1:        TMEM allocation; lane 0 issues the MMAs and commits
-//   warps 2..5:    epilogue, warp w reads TMEM lanes 32 (w mod 4) .. +31
+//   warps 2..9:    epilogue; warp w reads TMEM lanes 32 (w mod 4) .. +31 and
+//                  columns 64 ((w - 2) / 4) .. +63 of the tile
 // Every wait is bounded; on expiry the kernel records ST_TIMEOUT, stops
 // issuing, lets its copies and MMAs finish (bounded) and frees its TMEM.
 __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_constant__ BGArgs a) {
   extern __shared__ __align__(1024) unsigned char bg_raw[];
-  __shared__ __align__(8) uint64_t full[BG_MAXS], empty[BG_MAXS], tfull[2], tempty[2], drain;
+  __shared__ __align__(8) uint64_t full[BG_MAXS], empty[BG_MAXS], tfull[BG_NBUF], tempty[BG_NBUF], drain;
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int tmo;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -50,15 +53,15 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < BG_NBUF; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], 8);
     }
     mbar_init(&drain, 1);
     fence_mbar_init_cluster();
   }
   if (warp == 1) {
-    tmem_alloc(&tmem_sh, 2 * BG_MAXN);
+    tmem_alloc(&tmem_sh, 2 * BG_NBUF * BG_MAXN);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -96,40 +99,44 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
       // ----------------------------------------------------------- MMA issue
       const uint32_t idesc = umma_idesc_bf16(BG_BM, a.BN);
       const uint32_t sbase = smem_u32(smem);
-      int it = 0, lu = 0;
-      for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x, ++lu) {
+      int it = 0, gp = 0;   // K blocks and drain periods issued by this CTA
+      for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x) {
         const int t = u / a.NT, kc = t % a.KC;
         const int kb0 = kc * a.kc_blocks, kb1 = min(a.nkb, kb0 + a.kc_blocks);
-        const int b = lu & 1;
-        if (lu >= 2 && !mbar_wait<false>(&tempty[b], ((lu >> 1) - 1) & 1, a.limit_ns, a.status)) {
-          tmo = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(b * BG_MAXN);
-        uint32_t acc = 0;
-        for (int kb = kb0; kb < kb1; ++kb, ++it) {
-          const int s = it % S;
-          if (!mbar_wait<false>(&full[s], (it / S) & 1, a.limit_ns, a.status)) {
+        for (int pb = kb0; pb < kb1 && !tmo; pb += BG_DRAIN, ++gp) {
+          const int b = gp % BG_NBUF;
+          if (gp >= BG_NBUF && !mbar_wait<false>(&tempty[b], ((gp / BG_NBUF) - 1) & 1, a.limit_ns, a.status)) {
             tmo = 1;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = sbase + (uint32_t)s * sstride, sb = sa + a_bytes;
-#pragma unroll
-          for (int ks = 0; ks < BG_SW / 32; ++ks) {     // 16 BF16 = 32 bytes of K per MMA
-#pragma unroll
-            for (int pr = 0; pr < 6; ++pr) {
-              const uint64_t ad = sdesc_kmajor<BG_SW>(sa + kPlaneA[pr] * a_plane + ks * 32);
-              const uint64_t bd = sdesc_kmajor<BG_SW>(sb + kPlaneB[pr] * b_plane + ks * 32);
-              umma_bf16(d, ad, bd, idesc, acc);
-              acc = 1;
+          const uint32_t d = tmem + (uint32_t)(2 * b * BG_MAXN);   // main; corrections at + BG_MAXN
+          uint32_t acc = 0;
+          const int pe = min(kb1, pb + BG_DRAIN);
+          for (int kb = pb; kb < pe; ++kb, ++it) {
+            const int s = it % S;
+            if (!mbar_wait<false>(&full[s], (it / S) & 1, a.limit_ns, a.status)) {
+              tmo = 1;
+              break;
             }
+            tc_fence_after();
+            const uint32_t sa = sbase + (uint32_t)s * sstride, sb = sa + a_bytes;
+#pragma unroll
+            for (int ks = 0; ks < BG_SW / 32; ++ks) {     // 16 BF16 = 32 bytes of K per MMA
+#pragma unroll
+              for (int pr = 0; pr < 6; ++pr) {
+                const uint64_t ad = sdesc_kmajor<BG_SW>(sa + kPlaneA[pr] * a_plane + ks * 32);
+                const uint64_t bd = sdesc_kmajor<BG_SW>(sb + kPlaneB[pr] * b_plane + ks * 32);
+                // the main product in its own accumulator, the rest in the second
+                umma_bf16(pr == 0 ? d : d + BG_MAXN, ad, bd, idesc, pr == 0 ? (acc & 1u) : (acc >> 1));
+                acc |= pr == 0 ? 1u : 2u;
+              }
+            }
+            umma_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
-          umma_commit(&empty[s]);   // the stage is free once these MMAs have read it
+          if (tmo) break;
+          umma_commit(&tfull[b]);     // the period's sum is complete
         }
-        if (tmo) break;
-        umma_commit(&tfull[b]);     // the tile is complete
       }
       // no MMA may be in flight when the TMEM is freed
       umma_commit(&drain);
@@ -138,39 +145,58 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
     __syncwarp();
   } else {
     // ------------------------------------------------------------- epilogue
-    const int q = warp & 3;   // TMEM lane quarter of this warp
-    int lu = 0;
-    for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x, ++lu) {
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int c0 = ((warp - 2) >> 2) * 64;   // this warp's 64 columns of the tile
+    int gp = 0;
+    for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x) {
       const int nt = u % a.NT, t = u / a.NT, kc = t % a.KC, mt = t / a.KC;
-      const int b = lu & 1;
-      const bool ok = mbar_wait<false>(&tfull[b], (lu >> 1) & 1, a.limit_ns, a.status);
-      if (!__all_sync(0xffffffffu, ok)) {
+      const int kb0 = kc * a.kc_blocks, kb1 = min(a.nkb, kb0 + a.kc_blocks);
+      const int ncols = min(a.BN, a.N - nt * a.BN);
+      const int mine = min(64, ncols - c0);   // columns of this warp (<= 0: none)
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      float hi[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) hi[j] = 0.f;
+      bool ok = true;
+      for (int pb = kb0; pb < kb1; pb += BG_DRAIN, ++gp) {
+        const int b = gp % BG_NBUF;
+        ok = __all_sync(0xffffffffu, mbar_wait<false>(&tfull[b], (gp / BG_NBUF) & 1, a.limit_ns, a.status));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t col = (uint32_t)(2 * b * BG_MAXN + c0);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          if (h * 16 < mine) {   // uniform across the warp
+            uint32_t r[16], e[16];
+            tmem_ld16(lane_base + col + h * 16, r);              // main product
+            tmem_ld16(lane_base + col + BG_MAXN + h * 16, e);    // corrections
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              hi[h * 16 + j] += __uint_as_float(r[j]) + __uint_as_float(e[j]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (!ok) {
         tmo = 1;
         break;
       }
-      tc_fence_after();
       const int row = mt * BG_BM + q * 32 + lane;
-      const int ncols = min(a.BN, a.N - nt * a.BN);
-      float* dst = a.P + ((size_t)kc * a.N + (size_t)nt * a.BN) * a.M + row;
-      for (int c0 = 0; c0 < ncols; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BG_MAXN + c0), r);
-        tmem_ld_wait();
-        if (row < a.M) {
+      if (row < a.M) {
+        double* dst = a.P + ((size_t)kc * a.N + (size_t)nt * a.BN + c0) * a.M + row;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < ncols) __stcg(dst + (size_t)(c0 + j) * a.M, __uint_as_float(r[j]));
-        }
+        for (int j = 0; j < 64; ++j)
+          if (j < mine) __stcg(dst + (size_t)j * a.M, (double)hi[j]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 2 * BG_MAXN);
+  if (warp == 1) tmem_dealloc(tmem, 2 * BG_NBUF * BG_MAXN);
 }
 
 // ------------------------------------------------------------ plane splits
@@ -258,9 +284,9 @@ __global__ void reduce_link_kernel(const BatchIo io) {
   const int64_t plane = (int64_t)io.NB * io.nb * io.ldn;
   const int64_t chunk = (int64_t)io.m * io.n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < io.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float* src = io.P1 + (int64_t)s * io.n + i;
+    const double* src = io.P1 + (int64_t)s * io.n + i;
     double z = 0.0;
-    for (int kc = 0; kc < io.KC1; ++kc) z += (double)__ldcg(src + kc * chunk);   // fixed order
+    for (int kc = 0; kc < io.KC1; ++kc) z += __ldcg(src + kc * chunk);   // fixed order
     zout[i] = z;
     const double yd = io.y ? io.y[i] : 0.0;
     double r0, r1 = 0.0;
@@ -295,11 +321,11 @@ __global__ void reduce_grad_kernel(const BatchIo io) {
   if (io.st && io.st[io.active[s]].done) return;
   const int64_t chunk = (int64_t)io.NB * io.m * io.p;
   for (int q = 0; q < io.NB; ++q) {
-    const float* src = io.P2 + ((int64_t)q * io.m + s) * io.p;
+    const double* src = io.P2 + ((int64_t)q * io.m + s) * io.p;
     double* dst = io.part + ((int64_t)s * io.NB + q) * io.p;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < io.p; j += (int64_t)gridDim.x * blockDim.x) {
       double g = 0.0;
-      for (int kc = 0; kc < io.KC2; ++kc) g += (double)__ldcg(src + kc * chunk + j);
+      for (int kc = 0; kc < io.KC2; ++kc) g += __ldcg(src + kc * chunk + j);
       dst[j] = g;
     }
   }

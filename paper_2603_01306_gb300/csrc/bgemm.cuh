@@ -3,13 +3,26 @@
 // stored as three BF16 planes whose sum is the FP32 value exactly (8 + 8 + 8
 // significand bits).  Six BF16 products per element pair (the pairs of planes
 // whose significance sums to at most the third plane's) reproduce FP32
-// products to within 2^-23 relative, accumulated in FP32 in tensor memory.
+// products to within 2^-23 relative.
 //
-// The K range is cut into chunks; each work unit (M-tile, N-tile, K-chunk)
-// writes its FP32 partial tile, and a reduction kernel sums the chunks in
-// FP64 in a fixed order (deterministic), fused with what consumes the
-// product: the link of the loss (Z = X B) or the per-node gradient layout of
-// the p-phase (G = X' R).
+// Accumulation.  X' r cancels by several orders of magnitude near a node's
+// optimum (the gradient is small against the sum of the magnitudes of its
+// terms), and the tensor cores' FP32 accumulation loses about half an ulp of
+// the running sum per MMA (measured: its error grows like truncation, not
+// like rounding), so one FP32 accumulator over thousands of terms put the
+// duality gap's floor above 1e-6.  Two measures keep it near the fused
+// pass's: the main product (first planes of both operands) accumulates alone
+// in one TMEM accumulator, the five correction products (2^-8 smaller and
+// below, so their accumulation error is negligible) in a second one; and
+// both hold only BG_DRAIN K blocks (128 elements) before the epilogue warps
+// drain them into FP32 registers (round to nearest) while the MMAs fill the
+// other of two TMEM buffer pairs.
+//
+// The K range is also cut into chunks for parallelism; each work unit
+// (M-tile, N-tile, K-chunk) writes its partial tile in FP64 (hi + lo), and a
+// reduction kernel sums the chunks in FP64 in a fixed order (deterministic),
+// fused with what consumes the product: the link of the loss (Z = X B) or the
+// per-node gradient layout of the p-phase (G = X' R).
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -22,11 +35,13 @@ namespace relax {
 constexpr int BG_BM = 128;          // rows of A per tile (the MMA's M)
 constexpr int BG_SW = 64;           // bytes per tile row in shared memory (64-byte swizzle)
 constexpr int BG_BK = BG_SW / 2;    // K elements (BF16) per pipeline stage
-constexpr int BG_MAXN = 256;        // columns of D per tile (one MMA's N) at most
+constexpr int BG_MAXN = 128;        // columns of D per tile (one MMA's N) at most
+constexpr int BG_NBUF = 2;          // TMEM buffer pairs (main, corrections) of BG_MAXN columns each
+constexpr int BG_DRAIN = 4;         // K blocks accumulated in TMEM between drains
 constexpr int BG_PLANES = 3;
 constexpr int BG_MAXS = 8;          // pipeline stages at most
-constexpr int BG_THREADS = 192;     // producer warp, MMA warp, four epilogue warps
-constexpr int BG_MAXKC = 16;        // K chunks at most (partials are KC x N x M floats)
+constexpr int BG_THREADS = 320;     // producer warp, MMA warp, eight epilogue warps
+constexpr int BG_MAXKC = 16;        // K chunks at most (partials are KC x N x M doubles)
 
 struct BGArgs {
   CUtensorMap tmA;        // planes of A: dims {K, M, 3}, box {BG_BK, 128, 3}
@@ -35,7 +50,7 @@ struct BGArgs {
   int BN, NT, MT, KC;     // tile columns, N-tiles, M-tiles, K-chunks
   int kc_blocks, nkb;     // K blocks (of BG_BK) per chunk, K blocks over K
   int stages;
-  float* P;               // [KC][N][M] FP32 partial products
+  double* P;              // [KC][N][M] partial products (FP64)
   int* status;
   uint64_t limit_ns;
 };
@@ -76,9 +91,9 @@ struct BatchIo {
   const double* y;
   __nv_bfloat16* Bp;     // [3][nb][ldp] planes of the node points
   __nv_bfloat16* Rp;     // [3][NB nb][ldn] planes of the link (the second product's B)
-  const float* P1;       // [KC1][m][n] partials of Z = X B
+  const double* P1;      // [KC1][m][n] partials of Z = X B
   int KC1;
-  const float* P2;       // [KC2][NB m][p] partials of G = X' R
+  const double* P2;      // [KC2][NB m][p] partials of G = X' R
   int KC2;
   double* part;          // [m][NB][p] gradients per node (p-phase layout)
 };

@@ -5,11 +5,13 @@
 
 namespace relax {
 
-cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p) {
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack) {
   pl = PPlan{};
   pl.vdouble = vdouble;
-  pl.kernel = vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>)
-                      : reinterpret_cast<const void*>(&pphase_kernel<float, PEPT>);
+  if (backtrack && !vdouble) return cudaErrorNotSupported;   // the loop's vectors are FP64
+  pl.kernel = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT, true>)
+              : vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>)
+                        : reinterpret_cast<const void*>(&pphase_kernel<float, PEPT>);
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -84,10 +86,13 @@ static cudaError_t cluster_try(PPlan& pl, int64_t p, const void* kernel, int ept
   return cudaSuccess;
 }
 
-cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p) {
-  if (cluster_try(pl, p, reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>), PEPT, 16) == cudaSuccess)
-    return cudaSuccess;
-  return cluster_try(pl, p, reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>), PEPT_CLUSTER, 8);
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p, bool backtrack) {
+  const void* k4 = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT, true>)
+                             : reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>);
+  const void* k8 = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER, true>)
+                             : reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>);
+  if (cluster_try(pl, p, k4, PEPT, 16) == cudaSuccess) return cudaSuccess;
+  return cluster_try(pl, p, k8, PEPT_CLUSTER, 8);
 }
 
 cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st) {

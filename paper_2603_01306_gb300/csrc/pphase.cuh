@@ -78,6 +78,17 @@ struct IterState {
   int cut_rule;                 // dynamic termination of Sec. 5.3: 1 Phi <= cutoff, 2 Psi >= cutoff
   int cutoff_on;                // dynamic termination against `cutoff` (0: off)
   double cutoff;                // the incumbent's objective f(X b) + lambda2 ||b||^2
+  // step rule (backtracking, Beck Sec. 10.4.2): the current L, the rho of the
+  // prox that produced beta^t, and what the sufficient-decrease test of the
+  // pending trial point needs: <grad F(y), x - y>, ||x - y||^2 and X y (F(y)
+  // is summed from it with the next iteration's loss terms), with y and its
+  // gradient kept for a retry
+  double Lk, rho_last, dgy, dxy2;
+  void* y_keep;
+  void* gy_keep;
+  void* zy_keep;                // n: X y of the pending test
+  int bt_pending;               // 1: beta^t is a trial point whose test is pending
+  int backtracks;               // retries so far (each doubles L)
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
 
@@ -89,6 +100,9 @@ struct PArgs {
   double lambda2, M, step, rho, eta, tol;
   int max_iters;
   int stall_min;                // stall rule's least window (0: off)
+  int method;                   // 0 FISTA, 1 PGD (the convergence study of Sec. 5.2)
+  int restart_rule;             // 0 duality gap (Sec. 3.4), 1 function value, 2 none
+  int backtrack;                // 0 fixed step 1/L, 1 backtracking from L/64
   const int8_t* fix;            // NULL = root
   const void* part;             // [ncl][NB][p] doubles
   int ncl, NB;
@@ -169,8 +183,10 @@ __device__ __forceinline__ void cluster_barrier() {
 
 // TV: element type of the p-vectors (double in the loop and certification;
 // float or double for the standalone entry points).  EPT: elements per thread
-// (at most), so one CTA covers PBLOCK * EPT coordinates.
-template <typename TV, int EPT = PEPT>
+// (at most), so one CTA covers PBLOCK * EPT coordinates.  BT: the backtracking
+// step rule is compiled in (its test and retry cost registers that the
+// fixed-step loop does not pay).
+template <typename TV, int EPT = PEPT, bool BT = false>
 __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   using KG = unsigned long long;   // S1 keys: FP32 or FP64 bit patterns of |a|
   using KV = uint32_t;             // FP32 keys of the S2 / S3 thresholds
@@ -265,7 +281,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   const int64_t p = a.p;
   const double M = a.M;
   const double lam2 = a.lambda2;
-  const double rho = a.rho;
+  // the step of this iteration's prox: 1/L, or 1/L_k under backtracking
+  // (doubled below when the pending trial point fails its test)
+  double step = a.step;
+  double rho = a.rho;
+  if (BT && mode == PM_ITER && a.backtrack) {
+    step = 1.0 / st->Lk;
+    rho = 2.0 * lam2 * step;
+  }
   const TV Mv = (TV)M;
 
   // ---------------------------------------------------------------- P0
@@ -295,6 +318,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // sums: 0 sum_J1 H(a), 1 sum_J1 b^2, 2 sum_Jf |b|, 3 sum_Jf b^2, 4 nnz_Jf(b),
   //       5 domain violations, 6 non-finite, 7 sum_Jf H(a), 8 F(z), 9 -F*(-zeta)
   double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double fy_sum = 0.0;   // backtracking: F at the kept momentum point
   if (a.lossp) {
     // per-row loss terms written by the certification pass
     for (int64_t i = gt; i < a.n; i += nthr) {
@@ -302,17 +326,24 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       s0[9] += a.lossp[2 * i + 1];
     }
   } else if (mode == PM_ITER) {
-    // loss terms of Eq. 6-7 at z^t = X beta^t, zeta = -grad F(z^t), in FP64
+    // loss terms of Eq. 6-7 at z^t = X beta^t, zeta = -grad F(z^t), in FP64;
+    // with a backtracking test pending, also F at the kept momentum point
     const double* zt = static_cast<const double*>(st->z_cur);
+    const double* zy = (BT && a.backtrack && st->bt_pending) ? static_cast<const double*>(st->zy_keep) : nullptr;
     for (int64_t i = gt; i < a.n; i += nthr) {
       const double yi = a.y[i], zi = zt[i];
       if (a.loss == 0) {
         const double d = zi - yi, zeta = -2.0 * d;
         s0[8] += d * d;
         s0[9] += zeta * yi - 0.25 * zeta * zeta;
+        if (zy) {
+          const double dy = zy[i] - yi;
+          fy_sum += dy * dy;
+        }
       } else {
         s0[8] += softplus_neg(yi * zi);
         s0[9] += entropy_of(yi * zi);
+        if (zy) fy_sum += softplus_neg(yi * zy[i]);
       }
     }
   }
@@ -387,6 +418,22 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   const double Ftot = tot[8];
   const double Dtot = tot[9];
   const bool nonfinite = tot[6] > 0.0;
+  // Backtracking (Beck Sec. 10.4.2): beta^t = prox at y^{t-1} with step 1/L_k
+  // is accepted when F(X beta^t) <= F(y) + <grad F(y), beta^t - y> +
+  // L_k/2 ||beta^t - y||^2 (with an FP64 rounding slack of 1e-12 |F(y)|);
+  // otherwise L_k doubles and the prox is taken again from the kept y and
+  // its gradient, and this iteration evaluates nothing else.
+  bool retry = false;
+  if (BT && mode == PM_ITER && a.backtrack && st->bt_pending) {
+    gsum(&fy_sum, 1);   // uniform: every block reads the same pending flag
+    const double Fy = fy_sum;
+    const double rhs = Fy + st->dgy + 0.5 * st->Lk * st->dxy2 + 1e-12 * fmax(1.0, fabs(Fy));
+    retry = Ftot > rhs;
+    if (retry) {
+      step = 0.5 / st->Lk;
+      rho = 2.0 * lam2 * step;
+    }
+  }
 
   // ------------------------------------------------------ S1 / S2 setup
   bool s1 = false, s2 = false;
@@ -406,7 +453,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // z_j(c).  g then needs one classification at w instead of S2's rounds.
   const double c_prev = (mode == PM_ITER) ? st->c_last : 0.0;
   const bool w_known = mode == PM_ITER && st->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
-  const double w_closed = w_known ? fmin(c_prev / rho, M) : 0.0;
+  const double w_closed = w_known ? fmin(c_prev / st->rho_last, M) : 0.0;
   bool g_inf = false;
   if (need_b) {
     const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
@@ -428,6 +475,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   const KG kc1 = warm1 ? (key64 ? (KG)key_of(t1p) : (KG)key_of((float)t1p)) : (KG)0;
   const KV kc2 = warm2 ? key_of((float)w2p) : (KV)0;
   const int sh1 = key64 ? 29 : 0;   // FP64 keys: 29 more mantissa bits per FP32 step
+  if (retry) { s1 = false; s2 = false; warm1 = false; warm2 = false; }
   auto cand1 = [&](int q) { return warm1 ? warm_cand<KG>(kc1, lo1, hi1, q, sh1) : cand<KG>(lo1, hi1, q); };
   auto cand2 = [&](int q) { return warm2 ? warm_cand<KV>(kc2, lo2, hi2, q, 0) : cand<KV>(lo2, hi2, q); };
   while (s1 || s2) {
@@ -436,14 +484,26 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     const KV x2 = s2 ? cand2(lane) : (KV)0;
     const float w2 = from_key(x2, 0.f);
     const float inv2 = s2 ? 1.0f / w2 : 0.f;
-    for (int src = 0; src < 32; ++src) {
+    if (s1) {
+      // a key below the round's smallest candidate (candidates do not decrease
+      // with the lane) counts for no lane: only the keys at or above it are
+      // broadcast, which in a warm round are few
+      const KG x1min = cand1(0);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
-        if (s1) {
+        unsigned act = __ballot_sync(0xffffffffu, ka[e] >= x1min);
+        while (act) {
+          const int src = __ffs(act) - 1;
+          act &= act - 1u;
           const KG kv = __shfl_sync(0xffffffffu, ka[e], src);
           fld[F_S1] += (kv >= x1) ? 1ull : 0ull;
         }
-        if (s2) {
+      }
+    }
+    if (s2) {
+      for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
           const float b = __shfl_sync(0xffffffffu, bmf[e], src);
           if (b > 0.f) {
             const float z = b * inv2;
@@ -485,11 +545,11 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // ---------------------------------------------- exact S1 / S2 finishing
   // S1: t* = the kbar-th largest |a| (key lo1); TopSum = kbar H(t*) + sum (H(|a|) - H(t*))_+
   // S2: w on the bracket's piece, polished until the classification is stable.
-  const bool fin1 = need_a && kb > 0 && pb > kb;
+  const bool fin1 = need_a && kb > 0 && pb > kb && !retry;
   const double tstar = fin1 ? (key64 ? from_key((unsigned long long)lo1, 0.0)
                                      : (double)from_key((uint32_t)lo1, 0.f)) : 0.0;
   const double htstar = huber_d<double>(tstar, M);
-  bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb;
+  bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb && !retry;
   double wcur = pol2 ? (w_known ? w_closed : (double)from_key(hi2, 0.f)) : 0.0;
   double nprev = -1.0;
   const double wlo = (double)from_key(lo2, 0.f), whi = (double)from_key(hi2, 0.f);
@@ -568,7 +628,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0, cut_rule = 0;
   double stall_gap = 0.0;
   const int t = st ? st->iter : 0;
-  if (mode == PM_ITER) {
+  if (mode == PM_ITER && !retry) {
     const double tau = st->tau;
     gap_ref = st->gap_ref;
     have_ref = st->have_ref;
@@ -579,14 +639,22 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (phi < phi_best) { phi_best = phi; imp_p = true; }
     if (psi > psi_best) { psi_best = psi; imp_d = true; }
     const double gap = phi - psi;
-    if (!have_ref) {
-      if (isfinite(gap)) { gap_ref = gap; have_ref = 1; }
-    } else if (t >= 1 && gap <= gap_ref / a.eta) {
-      restart = true;
-      gap_ref = gap;
-      ++restarts;
+    if (a.method == 0 && a.restart_rule == 0) {         // duality-gap restart (Sec. 3.4)
+      if (!have_ref) {
+        if (isfinite(gap)) { gap_ref = gap; have_ref = 1; }
+      } else if (t >= 1 && gap <= gap_ref / a.eta) {
+        restart = true;
+        gap_ref = gap;
+        ++restarts;
+      }
+    } else if (a.method == 0 && a.restart_rule == 1) {  // function value (O'Donoghue and Candes)
+      if (t > 1 && phi > st->phi_t) {
+        restart = true;
+        ++restarts;
+      }
     }
-    if (t == 0) { mu = 0.0; tau_new = tau; }
+    if (a.method == 1) { mu = 0.0; tau_new = 1.0; }      // PGD: the prox step from beta^t itself
+    else if (t == 0) { mu = 0.0; tau_new = tau; }
     else if (restart) { mu = 0.0; tau_new = 1.0; }
     else {
       const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau * tau));
@@ -641,6 +709,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
 
   // ---------------------------------------------------------------- P1
   const bool do_prox = (mode == PM_PROX) || (mode == PM_ITER && !stop);
+  const bool keep = BT && mode == PM_ITER && a.backtrack;
+  if (do_prox && keep && !retry) {
+    // X y^t = (1 + mu) z^t - mu z^{t-1}, for the test of the next trial point
+    const double* zc = static_cast<const double*>(st->z_cur);
+    const double* zp = static_cast<const double*>(st->z_prev);
+    double* zk = static_cast<double*>(st->zy_keep);
+    for (int64_t i = gt; i < a.n; i += nthr) zk[i] = (1.0 + mu) * zc[i] - mu * zp[i];
+  }
   TV vv[EPT];
   TV mm[EPT];      // |v| on Jf
   float mmf[EPT];  // |v| rounded to FP32 (rounds)
@@ -650,7 +726,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (do_prox) {
     const TV* vin = static_cast<const TV*>(a.vin);
     const TV muv = (TV)mu;
-    const TV sv = (TV)a.step;
+    const TV sv = (TV)step;
+    TV* ykeep = keep ? static_cast<TV*>(st->y_keep) : nullptr;
+    TV* gkeep = keep ? static_cast<TV*>(st->gy_keep) : nullptr;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
@@ -658,12 +736,22 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       if (j >= p) continue;
       TV v;
       if (mode == PM_ITER) {
-        const TV b = bt[e];
-        const TV bp = bprev[j];
-        const TV y = b + muv * (b - bp);
+        TV y;
         double gyv;
-        if (a.loss == 0) gyv = (1.0 + mu) * gg[e] - mu * Gprev[j];
-        else gyv = (mu == 0.0) ? gg[e] : gy[e];
+        if (retry) {
+          y = ykeep[j];
+          gyv = (double)gkeep[j];
+        } else {
+          const TV b = bt[e];
+          const TV bp = bprev[j];
+          y = b + muv * (b - bp);
+          if (a.loss == 0) gyv = (1.0 + mu) * gg[e] - mu * Gprev[j];
+          else gyv = (mu == 0.0) ? gg[e] : gy[e];
+          if (keep) {
+            ykeep[j] = y;
+            gkeep[j] = (TV)gyv;
+          }
+        }
         v = y - sv * (TV)gyv;
       } else {
         v = vin[j];
@@ -709,9 +797,17 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       const double cqd = (double)cq;
       const double wq = fmin(cqd / rho, M);
       const float invw = (float)(1.0 / wq);
-      for (int src = 0; src < 32; ++src) {
+      // |v_j| at or below the round's smallest candidate adds nothing for any
+      // lane (and T^-1(|v_j|) <= |v_j| neither): only the coordinates above
+      // it are broadcast, which after the first round are about the top kbar
+      // and the bracket's
+      const float cmin = from_key(cand3(0), 0.f);
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) {
+      for (int e = 0; e < EPT; ++e) {
+        unsigned act = __ballot_sync(0xffffffffu, mmf[e] > cmin);
+        while (act) {
+          const int src = __ffs(act) - 1;
+          act &= act - 1u;
           const float m = __shfl_sync(0xffffffffu, mmf[e], src);
           const float tv = __shfl_sync(0xffffffffu, ti[e], src);
           if (m > cq) {
@@ -773,8 +869,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
 
   // ---------------------------------------------------------------- P2
+  double tst_out[2] = {0.0, 0.0};
   if (do_prox) {
-    TV* out = mode == PM_ITER ? static_cast<TV*>(st->beta_prev) : static_cast<TV*>(a.vout);
+    // the next iterate goes to the buffer that becomes beta_cur after the
+    // rotation; a retried trial point replaces the rejected one in place
+    TV* out = mode == PM_ITER ? static_cast<TV*>(retry ? st->beta_cur : st->beta_prev) : static_cast<TV*>(a.vout);
+    double tst[2] = {0.0, 0.0};   // backtracking: <grad F(y), x - y>, ||x - y||^2
     const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
     double cnt[2] = {0, 0};
     // Standalone prox: a non-finite input, or a bounded wait of this block
@@ -800,6 +900,16 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         }
       }
       out[j] = (TV)b;
+      if (keep) {   // y^t and its gradient as P1 kept them (this thread's own writes)
+        const double d = b - (double)static_cast<const TV*>(st->y_keep)[j];
+        tst[0] += (double)static_cast<const TV*>(st->gy_keep)[j] * d;
+        tst[1] += d * d;
+      }
+    }
+    if (keep) {
+      gsum(tst, 2);
+      tst_out[0] = tst[0];
+      tst_out[1] = tst[1];
     }
     if (mode == PM_PROX && a.counts) {
       gsum(cnt, 2);
@@ -818,9 +928,25 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   barrier();   // everyone is done with the round accumulators
   if (lbk == 0) {
     for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
-    if (tid == 0) {
+    if (tid == 0 && mode == PM_ITER && retry) {
+      // a rejected trial point: the same iteration again, with L doubled
+      st->Lk *= 2.0;
+      st->rho_last = rho;
+      st->dgy = tst_out[0];
+      st->dxy2 = tst_out[1];
+      st->bt_pending = 1;
+      st->backtracks += 1;
+      st->c_last = c;
+      st->bar_base = bar0 + (unsigned long long)nbar * nbk;
+    } else if (tid == 0) {
       if (mode == PM_ITER) {
         if (nonfinite) atomicCAS(a.status, ST_OK, ST_NUMERIC);
+        st->rho_last = rho;
+        if (a.backtrack && !stop) {
+          st->dgy = tst_out[0];
+          st->dxy2 = tst_out[1];
+          st->bt_pending = 1;
+        }
         st->phi_t = phi;
         st->psi_t = psi;
         st->g_t = gval;
@@ -857,7 +983,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
           st->ps.zprev = st->z_prev;
           // tentative momentum for the pass at beta^{t+1} (the no-restart value)
           const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tau_new * tau_new));
-          st->ps.mom = (tau_new - 1.0) / tn;
+          st->ps.mom = a.method == 1 ? 0.0 : (tau_new - 1.0) / tn;
         }
         st->bar_base = bar0 + (unsigned long long)nbar * nbk;
       }

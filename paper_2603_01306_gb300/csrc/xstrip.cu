@@ -39,8 +39,7 @@ static int xs_tv(int vec) { return vec == 2 ? 6 : vec == 4 ? 6 : vec == 8 ? 3 : 
 //    row), chosen to keep the most SMs busy (Gc strips x Gr row groups), at
 //    least 2 KB wide where possible;
 //  * a strip is nbox tensor boxes of `inner` <= 256 columns;
-//  * blocks of B <= 16 rows so that a stage is about 40 KB; 3 + 3 (or 3 + 4)
-//    stages;
+//  * blocks of B <= 16 rows so that a stage is about 40 KB; 3 + 3 stages;
 //  * phase A may lead phase B by `lag` blocks: about 64 MB of X in L2.
 // RELAX_XS="B,SA,SB,lag,vps" overrides for tuning runs (0 keeps a default).
 cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p) {
@@ -98,11 +97,10 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
     return (size_t)(sa + sb) * (size_t)(nbox * boxb(b)) + fixed <= (size_t)optin;
   };
   while (B > 1 && !fits(B, 3, 3)) --B;
-  int SA = 3, SB = 3;   // 1 + SA + SB warps <= 8
-  if (fits(B, 3, 4)) SB = 4;
+  int SA = 3, SB = 3;   // 2 + SA + SB warps <= 8
   if (SA_f > 0) SA = std::min(SA_f, XS_MAXS);
   if (SB_f > 0) SB = std::min(SB_f, XS_MAXS);
-  if (1 + SA + SB > XS_MAXT / 32 || !fits(B, SA, SB)) return cudaErrorNotSupported;
+  if (2 + SA + SB > XS_MAXT / 32 || !fits(B, SA, SB)) return cudaErrorNotSupported;
   pl.B = (int)B;
   pl.boxb = (int)boxb(B);
   pl.nblk = (int)((n + B - 1) / B);
@@ -112,7 +110,7 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   const double row_bytes = (double)p * es;
   pl.lag = lag_f > 0 ? lag_f : (int)std::max(4.0, std::min(64.0, 64.0e6 / (B * row_bytes * pl.Gr)));
   pl.grid = pl.Gc * pl.Gr;
-  pl.threads = 32 * (1 + SA + SB);   // producers, SA dot, SB axpy
+  pl.threads = 32 * (2 + SA + SB);   // two producers, SA dot, SB axpy
   // the combine of the axpy warps' strip sums reuses the rings
   const size_t ring = (size_t)(SA + SB) * nbox * pl.boxb;
   const size_t comb = (size_t)SB * NB * pl.sw * sizeof(double);

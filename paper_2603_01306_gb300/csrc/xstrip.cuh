@@ -14,7 +14,7 @@
 //  * lane 0 of warp 0 streams the CTA's strip tiles of its blocks from HBM into
 //    ring A (SA stages; a tile is nbox 2-D tensor boxes of B rows x `inner`
 //    columns, loaded by TMA, which zero-fills columns >= p and rows >= n);
-//    lane 16 of warp 0 loads the same tiles again, from L2, into ring B (SB
+//    lane 0 of warp 1 loads the same tiles again, from L2, into ring B (SB
 //    stages);
 //  * SA "dot" warps (warp a owns stage a of ring A): per row the strip's partial
 //    dot product with beta, added to the row's z in 64-bit fixed point
@@ -48,7 +48,7 @@ namespace relax {
 
 constexpr int XS_MAXS = 4;        // stages per ring at most (= warps per phase)
 constexpr int XS_MAXB = 16;       // rows per block at most (one butterfly group)
-constexpr int XS_MAXT = 256;      // 1 + SA + SB warps: at most two per scheduler
+constexpr int XS_MAXT = 256;      // 2 + SA + SB warps: at most two per scheduler
 // 16-byte vectors of the strip per lane: a lane holds the same number of
 // accumulators (24 FP32 or 12 FP64 columns, 24/32 for 16/8-bit X) for every type
 template <int VEC> struct XSShape {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   // phase-B accumulators (used by the axpy warps only)
   TA acc[NB][TV][VEC];
   float ahi[kF32 ? NB : 1][TV][VEC], alo[kF32 ? NB : 1][TV][VEC];
-  const bool axpy = warp >= 1 + a.SA && warp < 1 + a.SA + a.SB;
+  const bool axpy = warp >= 2 + a.SA && warp < 2 + a.SA + a.SB;
 
   if (warp == 0) {
     // ------------------------------------------------ producer A: HBM -> ring A
@@ -321,8 +321,10 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       for (int k = (issued > a.SA ? issued - a.SA : 0); k < issued; ++k)
         mbar_wait<false>(&fullA[k % a.SA], (k / a.SA) & 1, a.limit_ns, a.status);
     }
-    // ------------------------------------------------- producer B: L2 -> ring B
-    if (lane == 16) {
+  } else if (warp == 1) {
+    // ---------------------------------- producer B: L2 -> ring B (its own warp,
+    // so that its waits and copies never serialise with producer A's)
+    if (lane == 0) {
       const uint64_t pol = policy_evict_first();
       int issued = 0;
       for (int k = 0; k < kloc; ++k) {
@@ -338,9 +340,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       for (int k = (issued > a.SB ? issued - a.SB : 0); k < issued; ++k)
         mbar_wait<false>(&fullB[k % a.SB], (k / a.SB) & 1, a.limit_ns, a.status);
     }
-  } else if (warp < 1 + a.SA) {
+  } else if (warp < 2 + a.SA) {
     // ------------------------------------------------ phase A: strip dot products
-    const int st = warp - 1;
+    const int st = warp - 2;
     TA bv[NF][TV][VEC];
 #pragma unroll
     for (int t = 0; t < TV; ++t) {
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
     }
   } else if (axpy) {
     // ------------------------------------------------ phase B: X' r over the strip
-    const int st = warp - 1 - a.SA;
+    const int st = warp - 2 - a.SA;
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   const int wcols = nvs * VEC;
   double* comb = reinterpret_cast<double*>(smem);   // [SB][NB][wcols] strip sums of the axpy warps
   if (axpy) {
-    const int st = warp - 1 - a.SA;
+    const int st = warp - 2 - a.SA;
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll

@@ -39,7 +39,8 @@ def test_create_rejects_invalid_arguments(bad):
 
 
 @pytest.mark.parametrize("field,value", [("M", -1.0), ("M", math.nan), ("eta", -2.0), ("lipschitz", -1.0),
-                                         ("max_iters", -5), ("watchdog_ms", -1), ("chunk", -3)])
+                                         ("max_iters", -5), ("watchdog_ms", -1), ("chunk", -3), ("method", 2),
+                                         ("method", -1), ("restart", 3), ("step_rule", 2), ("step_rule", -1)])
 def test_create_rejects_invalid_options(field, value):
     o = B.make_options()
     setattr(o, field, value)
@@ -69,11 +70,11 @@ def test_solve_and_batch_reject_invalid_arguments():
     assert lib.relax_solve_batch(FAKE, 2, None, None, 0.0, FAKE, res_arr) == EINVAL
     assert lib.relax_solve_batch(FAKE, 2, None, None, 1e-6, None, res_arr) == EINVAL
     assert lib.relax_solve_batch(FAKE, 2, None, None, 1e-6, FAKE, None) == EINVAL
-    assert lib.relax_batch_xpass(None, 2, FAKE, FAKE, FAKE) == EINVAL
-    assert lib.relax_batch_xpass(FAKE, 0, FAKE, FAKE, FAKE) == EINVAL
-    assert lib.relax_batch_xpass(FAKE, 2, None, FAKE, FAKE) == EINVAL
-    assert lib.relax_batch_xpass(FAKE, 2, FAKE, None, FAKE) == EINVAL
-    assert lib.relax_batch_xpass(FAKE, 2, FAKE, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(None, 2, FAKE, FAKE, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 0, FAKE, FAKE, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, None, FAKE, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, FAKE, None, FAKE, None) == EINVAL
+    assert lib.relax_batch_xpass(FAKE, 2, FAKE, FAKE, None, None) == EINVAL
     assert lib.relax_set_cutoff(None, 1.0) == EINVAL
     assert lib.relax_set_cutoff(FAKE, math.nan) == EINVAL
     assert lib.relax_xpass(None, FAKE, None, FAKE, None) == EINVAL

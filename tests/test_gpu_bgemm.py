@@ -62,11 +62,12 @@ def test_batch_products_f32_match_fp64(lib, shape):
     z, g = h.batch_xpass(torch.tensor(B, device="cuda"))
     z, g = z.cpu().numpy(), g.cpu().numpy()
     z_ref = B64 @ X64.T                          # [nb][n]
-    _check(z, z_ref, np.abs(B64) @ np.abs(X64).T, p)
-    # the second product is taken of the device's own z (FP64 values, split exactly
+    rz = _check(z, z_ref, np.abs(B64) @ np.abs(X64).T, p)
+    # the second product is taken of the device's own z (FP64 values, split
     # to 24 bits): compare with X' applied to that z
     g_ref = z @ X64
-    _check(g, g_ref, np.abs(z) @ np.abs(X64), n)
+    rg = _check(g, g_ref, np.abs(z) @ np.abs(X64), n)
+    print(f"shape {shape}: RMS relative error z {rz:.2e}, g {rg:.2e}")
     # deterministic: fixed chunking and fixed-order FP64 sums
     z2, g2 = h.batch_xpass(torch.tensor(B, device="cuda"))
     assert np.array_equal(z2.cpu().numpy(), z) and np.array_equal(g2.cpu().numpy(), g)
