@@ -5,8 +5,14 @@
 // include/warmstart.h); with bf16 != 0 every kernel evaluates the network
 // with the trainable entries rounded to BF16, accumulating in FP32.
 //
-// forward: one thread per row, weights in shared memory, layer 2 fused with
-//          the output layer (no 64-wide activation leaves the registers).
+// forward: BF16 weights: the 64 x 64 layer on the tensor cores (mma.sync
+//          m16n8k16, BF16 operands, FP32 accumulation), 16 rows per warp:
+//          each lane computes layer 1 for the A-fragment entries it holds and
+//          splits them into three BF16 planes (exactly the FP32 value), so the
+//          products are exact and only the FP32 sums round; layer 2's bias,
+//          ReLU and the output layer follow on the accumulator fragments.
+//          FP32 weights (the reference build of the network): one thread per
+//          row on the CUDA cores, layer 2 fused with the output layer.
 // grad:    tiles of 128 rows per CTA; per row the forward and the backward
 //          sweep run in registers and leave h1, h2, dL/da2, dL/da1 in shared
 //          memory; the CTA then folds the tile into its weight-gradient
@@ -79,6 +85,112 @@ __device__ __forceinline__ float dot64(const float* w, const float* h) {
     a3 = fmaf(w[k + 3], h[k + 3], a3);
   }
   return (a0 + a1) + (a2 + a3);
+}
+
+// ---- tensor-core forward (BF16 weights)
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+// x = p0 + p1 + p2 exactly (8 + 8 + 8 significand bits of an FP32 value)
+__device__ __forceinline__ void split3_f32(float x, __nv_bfloat16 (&q)[3]) {
+  q[0] = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(q[0]);
+  q[1] = __float2bfloat16_rn(r1);
+  q[2] = __float2bfloat16_rn(r1 - __bfloat162float(q[1]));
+}
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int MMA_WARPS = 4;
+constexpr int W2LD = NH + 8;   // padded row of W2 in shared memory: the 8 row groups hit distinct banks
+
+__global__ void __launch_bounds__(32 * MMA_WARPS) mlp_forward_mma_kernel(const float* theta, const float* feat,
+                                                                        const float* base, int64_t rows, float* out) {
+  __shared__ SW s;
+  __shared__ __align__(16) __nv_bfloat16 W2b[NH * W2LD];   // W2 [o][h], exact in BF16
+  load_weights(s, theta, 1);
+  for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) W2b[(i / NH) * W2LD + i % NH] = __float2bfloat16_rn(s.W2[i]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;   // fragment row group, column pair
+  const int64_t ntiles = (rows + 15) / 16;
+  for (int64_t tile = (int64_t)blockIdx.x * MMA_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * MMA_WARPS) {
+    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+    float x0[NIN], x1[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+      x0[i] = r0 < rows ? (feat[r0 * NIN + i] - s.shift[i]) * s.iscale[i] : 0.f;
+      x1[i] = r1 < rows ? (feat[r1 * NIN + i] - s.shift[i]) * s.iscale[i] : 0.f;
+    }
+    // A fragments of layer 2's input h1 (rows r0, r1 x 64 hidden units), three planes
+    uint32_t A[3][4][4];
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {            // columns 2 t4 (+1) and 2 t4 + 8 (+1)
+        __nv_bfloat16 q00[3], q01[3], q10[3], q11[3];
+        const int h = kc * 16 + 2 * t4 + 8 * hh;
+        float a00 = s.b1[h], a01 = s.b1[h + 1], a10 = s.b1[h], a11 = s.b1[h + 1];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) {
+          a00 = fmaf(s.W1[h * NIN + i], x0[i], a00);
+          a01 = fmaf(s.W1[(h + 1) * NIN + i], x0[i], a01);
+          a10 = fmaf(s.W1[h * NIN + i], x1[i], a10);
+          a11 = fmaf(s.W1[(h + 1) * NIN + i], x1[i], a11);
+        }
+        split3_f32(a00 > 0.f ? a00 : 0.f, q00);
+        split3_f32(a01 > 0.f ? a01 : 0.f, q01);
+        split3_f32(a10 > 0.f ? a10 : 0.f, q10);
+        split3_f32(a11 > 0.f ? a11 : 0.f, q11);
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          A[pl][kc][2 * hh] = pack_bf16(q00[pl], q01[pl]);       // row g
+          A[pl][kc][2 * hh + 1] = pack_bf16(q10[pl], q11[pl]);   // row g + 8
+        }
+      }
+    }
+    float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < NH / 8; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      const __nv_bfloat16* wrow = W2b + (nt * 8 + g) * W2LD;   // output unit nt*8+g, k contiguous
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + kc * 16 + 2 * t4);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + kc * 16 + 2 * t4 + 8);
+#pragma unroll
+        for (int pl = 2; pl >= 0; --pl) mma_bf16_16816(d, A[pl][kc], b0, b1);   // small planes first
+      }
+      // d: (row g, cols o, o+1), (row g + 8, cols o, o+1), o = nt*8 + 2 t4
+      const int o = nt * 8 + 2 * t4;
+      const float h00 = d[0] + s.b2[o], h01 = d[1] + s.b2[o + 1];
+      const float h10 = d[2] + s.b2[o], h11 = d[3] + s.b2[o + 1];
+      if (h00 > 0.f) y0 = fmaf(s.w3[o], h00, y0);
+      if (h01 > 0.f) y0 = fmaf(s.w3[o + 1], h01, y0);
+      if (h10 > 0.f) y1 = fmaf(s.w3[o], h10, y1);
+      if (h11 > 0.f) y1 = fmaf(s.w3[o + 1], h11, y1);
+    }
+    // the four lanes of a row group hold disjoint output units: sum them
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+    if (t4 == 0) {
+      if (r0 < rows) {
+        const float y = s.b3 + y0;
+        out[r0] = base ? (feat[r0 * NIN + 2] < -0.5f ? 0.f : base[r0] + y) : y;
+      }
+      if (r1 < rows) {
+        const float y = s.b3 + y1;
+        out[r1] = base ? (feat[r1 * NIN + 2] < -0.5f ? 0.f : base[r1] + y) : y;
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(FWD_THREADS) mlp_forward_kernel(const float* theta, int bf16, const float* feat,
@@ -286,10 +398,16 @@ relax_status relax_mlp_forward(const float* theta, int32_t bf16, const float* fe
                                float* out, void* stream) {
   if (!theta || !feat || !out || rows < 0) return RELAX_EINVAL;
   if (rows == 0) return RELAX_OK;
+  if (bf16) {   // BF16 weights: the tensor-core forward, grid-stride over 16-row tiles
+    const int64_t tiles = (rows + 15) / 16;
+    const int64_t want = (tiles + MMA_WARPS - 1) / MMA_WARPS;
+    const unsigned grid = (unsigned)(want < 8 * sm_count() ? want : 8 * sm_count());
+    mlp_forward_mma_kernel<<<grid, 32 * MMA_WARPS, 0, (cudaStream_t)stream>>>(theta, feat, base, rows, out);
+    return cuda_status(cudaGetLastError());
+  }
   const int64_t grid = (rows + FWD_THREADS - 1) / FWD_THREADS;
   if (grid > INT32_MAX) return RELAX_ENOTSUP;
-  mlp_forward_kernel<<<(unsigned)grid, FWD_THREADS, 0, (cudaStream_t)stream>>>(theta, bf16 ? 1 : 0, feat, base, rows,
-                                                                              out);
+  mlp_forward_kernel<<<(unsigned)grid, FWD_THREADS, 0, (cudaStream_t)stream>>>(theta, 0, feat, base, rows, out);
   return cuda_status(cudaGetLastError());
 }
 

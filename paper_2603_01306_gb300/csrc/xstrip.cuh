@@ -454,9 +454,11 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           atomicAdd(&a.zfix[(size_t)f * n + r0 + (lane >> 1)], (unsigned long long)q);
         }
       }
-      __threadfence();
+      // the block is counted with release semantics: after the warp barrier the
+      // lanes' fixed-point additions above are ordered before the increment
+      // that phase B's acquire-loads observe (cheaper than a full fence)
       __syncwarp();
-      if (lane == 0) atomicAdd(&a.cnt[b], 1u);
+      if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.cnt[b]) : "memory");
     }
   } else if (axpy) {
     // ------------------------------------------------ phase B: X' r over the strip
