@@ -172,6 +172,12 @@ def run_ours(args):
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
+    if args.workload == BNB_WORKLOAD:
+        relax.load()
+        if rank != 0:
+            return None
+        return {"metric": "branch and bound with the learned warm start vs the parent start", **run_bnb(device),
+                "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded AR(1) Gaussian design)"}
     if args.workload == BATCH_WORKLOAD:
         # the batched-node workload alone (one JSON object, rank 0)
         relax.load()
@@ -372,6 +378,67 @@ def run_batch(device, workload=BATCH_WORKLOAD, reps=2, singles=16):
             "products": "the library's tcgen05 kernel on BF16 planes of X, X' and the node operands "
                         "(FP32-accurate products, TMEM sums drained every 128 terms, FP64 sums of the K chunks); "
                         "each round of 16 iterations is one CUDA graph"}
+
+
+BNB_WORKLOAD = "bnb_2000x5000_f32"
+
+
+def run_bnb(device, workload=BNB_WORKLOAD, gen_nodes=20000, eval_nodes=20000, batch=64, epochs=3, seed=0):
+    """The learned warm start at its configuration (X 2000 x 5000, rho 0.8,
+    k 15, lambda2 0.2, LS): a batched best-first BnB from the parent start
+    records its (parent, child) node solves; the network is trained on them on
+    the device by the library's kernels (the last tenth of the pairs held
+    out); then the BnB runs again from scratch with the parent start and with
+    the learned start (Phi fallback), and both runs are reported: nodes,
+    FISTA iterations, wall time, certified or not, incumbent and bound."""
+    import numpy as np
+    import torch
+    import paper_2603_01306_gb300 as relax
+    from paper_2603_01306_gb300 import bnb
+    from paper_2603_01306_gb300.warmstart import WarmStartNet
+    import synth
+    w = synth.WORKLOADS[workload]
+    X, y = synth.make_problem_gpu(w, device=device)
+    h = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M)
+    t0 = time.perf_counter()
+    gen = bnb.run(h, w.k, max_nodes=gen_nodes, gap_tol=GAP_TOL, warm="parent", record=True, batch=batch)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    pairs = gen.pairs
+    gen.pairs = []
+    cut = int(0.9 * len(pairs))
+    t0 = time.perf_counter()
+    Ftr, Ttr = bnb.training_rows(h, pairs[:cut])
+    Fte, Tte = bnb.training_rows(h, pairs[cut:])
+    del pairs
+    net = WarmStartNet(seed=seed, bf16=True)
+    net.set_standardisation(Ftr[::97])
+    mse_parent = net.loss_of(Fte, Tte)
+    net.fit(Ftr, Ttr, epochs=epochs, batch=1 << 16, lr=1e-3, seed=seed)
+    mse_learned = net.loss_of(Fte, Tte)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = int(Ftr.shape[0])
+    del Ftr, Ttr, Fte, Tte
+    runs = {}
+    for warm in ("parent", "learned"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = bnb.run(h, w.k, max_nodes=eval_nodes, gap_tol=GAP_TOL, warm=warm, net=net, batch=batch)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        runs[warm] = {"nodes": st.nodes, "iterations": st.iters, "seconds": dt, "nodes_per_s": st.nodes / dt,
+                      "certified": st.certified, "incumbent": st.incumbent, "best_bound": st.best_bound,
+                      "rel_gap": (st.incumbent - st.best_bound) / max(1.0, abs(st.incumbent)),
+                      "learned_used": st.learned_used, "fallbacks": st.fallbacks,
+                      "rule1_branch": st.cut_branch, "rule2_prune": st.cut_prune}
+    h.close()
+    return {"workload": workload, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2, "rho": w.rho,
+            "generation": {"nodes": gen.nodes, "seconds": t_gen, "certified": gen.certified},
+            "training": {"rows": rows, "pairs": cut, "epochs": epochs, "seconds": t_train,
+                         "heldout_mse_parent_start": mse_parent, "heldout_mse_learned_start": mse_learned},
+            "bnb_parent_start": runs["parent"], "bnb_learned_start": runs["learned"],
+            "iterations_ratio_learned_over_parent": runs["learned"]["iterations"] / max(1, runs["parent"]["iterations"])}
 
 
 def oracle_sample(Xh, yh, w, L, sample_iters):
