@@ -212,8 +212,7 @@ struct relax_handle {
   __nv_bfloat16* bxt = nullptr;
   int64_t ldbp = 0, ldbn = 0;
   CUtensorMap tm_bx{}, tm_bxt{};
-  int bg_kc[2][BG_MAXN / 16 + 1] = {};
-  cudaEvent_t ev_t[2] = {nullptr, nullptr};   // timing of the chunk candidates and of the first product
+  cudaEvent_t ev_t[2] = {nullptr, nullptr};   // timing of the first product (relax_batch_xpass)
   cudaEvent_t ev_p[2] = {nullptr, nullptr};   // timing of the second product (relax_batch_xpass)
   int dev = 0;
   cudaStream_t stream = nullptr;
@@ -1436,51 +1435,10 @@ relax_status ensure_planes(relax_handle* h) {
   return RELAX_OK;
 }
 
-// The K chunks of one product of a batched solve: chosen once per handle,
-// product and column tile width by timing the candidates (about one to four
-// work units per SM) on the call's own operands, the fastest kept.
-relax_status tune_chunks(relax_handle* h, int which, BGArgs a, int M, int N, int K, BGPlan* best) {
-  BGPlan pl;
-  CU(bgemm_plan(pl, M, N, K, 0));
-  int& slot = h->bg_kc[which][pl.BN / 16];
-  if (slot > 0) {
-    CU(bgemm_plan(*best, M, N, K, slot));
-    return RELAX_OK;
-  }
-  int nsm = 0;
-  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
-  const int tiles = pl.MT * pl.NT;
-  cudaEvent_t e0 = h->ev_t[0], e1 = h->ev_t[1];
-  float best_ms = INFINITY;
-  int best_kc = pl.KC, last_kc = -1;
-  for (int w = 1; w <= 4; ++w) {
-    BGPlan c;
-    CU(bgemm_plan(c, M, N, K, (w * nsm + tiles - 1) / tiles));
-    if (c.KC == last_kc) continue;
-    last_kc = c.KC;
-    a.BN = c.BN; a.NT = c.NT; a.MT = c.MT; a.KC = c.KC; a.kc_blocks = c.kc_blocks; a.nkb = c.nkb;
-    a.stages = c.stages;
-    CU(bgemm_launch(c, a, h->stream));   // warm-up
-    CU(cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < 2; ++r) CU(bgemm_launch(c, a, h->stream));
-    CU(cudaEventRecord(e1, h->stream));
-    CU(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best_kc = c.KC;
-    }
-  }
-  slot = best_kc;
-  CU(bgemm_plan(*best, M, N, K, best_kc));
-  return RELAX_OK;
-}
-
 void fill_bgargs(BGArgs& a, const BGPlan& pl, double* P, int* status, uint64_t limit_ns) {
   a.M = pl.M; a.N = pl.N; a.K = pl.K;
-  a.BN = pl.BN; a.NT = pl.NT; a.MT = pl.MT; a.KC = pl.KC;
-  a.kc_blocks = pl.kc_blocks; a.nkb = pl.nkb; a.stages = pl.stages;
+  a.BN = pl.BN; a.NT = pl.NT; a.MT = pl.MT;
+  a.nkb = pl.nkb; a.stages = pl.stages;
   a.P = P;
   a.status = status;
   a.limit_ns = limit_ns;
@@ -1673,16 +1631,12 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     BGArgs a1{}, a2{};
     BatchIo io{};
     if (!f64) {
-      BTRYC(bgemm_plan(pl1, (int)n, m, (int)p, 0));
-      BTRYC(bgemm_plan(pl2, (int)p, NB * m, (int)n, 0));
+      BTRYC(bgemm_plan(pl1, (int)n, m, (int)p));
+      BTRYC(bgemm_plan(pl2, (int)p, NB * m, (int)n));
       a1.tmA = h->tm_bx;
       a2.tmA = h->tm_bxt;
       BTRYC(bgemm_encode(&a1.tmB, Bp, p, m, h->ldbp, nb, pl1.BN));
       BTRYC(bgemm_encode(&a2.tmB, Rp, n, (int64_t)NB * m, h->ldbn, (int64_t)NB * nb, pl2.BN));
-      fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
-      fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
-      BTRY(tune_chunks(h, 0, a1, (int)n, m, (int)p, &pl1));
-      BTRY(tune_chunks(h, 1, a2, (int)p, NB * m, (int)n, &pl2));
       fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
       fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
       io.st = dst;
@@ -1699,9 +1653,9 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
       io.Bp = Bp;
       io.Rp = Rp;
       io.P1 = P1;
-      io.KC1 = pl1.KC;
+      io.s1 = pl1.split();
       io.P2 = P2;
-      io.KC2 = pl2.KC;
+      io.s2 = pl2.split();
       io.part = part;
     }
     const dim3 gp((unsigned)std::min<int64_t>(64, (p + 255) / 256), (unsigned)m);
@@ -2046,8 +2000,8 @@ extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const voi
     to_f64_kernel<<<grid_for((int64_t)nb * p), 256, 0, h->stream>>>(points, 0, bsrc, (int64_t)nb * p);
     CU(cudaGetLastError());
     BGPlan pl1, pl2;
-    CU(bgemm_plan(pl1, (int)n, nb, (int)p, 0));
-    CU(bgemm_plan(pl2, (int)p, nb, (int)n, 0));
+    CU(bgemm_plan(pl1, (int)n, nb, (int)p));
+    CU(bgemm_plan(pl2, (int)p, nb, (int)n));
     BGArgs a1{}, a2{};
     a1.tmA = h->tm_bx;
     a2.tmA = h->tm_bxt;
@@ -2069,9 +2023,9 @@ extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const voi
     io.Bp = Bp;
     io.Rp = Rp;
     io.P1 = P1;
-    io.KC1 = pl1.KC;
+    io.s1 = pl1.split();
     io.P2 = P2;
-    io.KC2 = pl2.KC;
+    io.s2 = pl2.split();
     io.part = g_out;              // NB = 1: part[s][0][j] = g_out[s * p + j]
     CU(batch_pack(io, h->stream));
     CU(cudaEventRecord(h->ev_t[0], h->stream));

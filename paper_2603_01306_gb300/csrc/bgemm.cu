@@ -13,21 +13,32 @@ namespace relax {
 
 namespace {
 
-// (plane of A, plane of B) of the six products kept: significance 2^0, 2^-8
-// (twice), 2^-16 (three times); the dropped ones are below 2^-23 relative
-__constant__ int kPlaneA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int kPlaneB[6] = {0, 1, 0, 2, 1, 0};
+// One piece of a CTA's range: K blocks [kb0, kb1) of tile t, written to
+// partial slot `slot` of the tile.
+struct BGSeg {
+  int t, kb0, kb1, slot;
+};
+__device__ __forceinline__ BGSeg bg_seg(const BGArgs& a, int64_t i, int64_t iend, int64_t T) {
+  BGSeg g;
+  g.t = (int)(i / a.nkb);
+  const int64_t t0 = (int64_t)g.t * a.nkb;
+  g.kb0 = (int)(i - t0);
+  g.kb1 = (int)(min(iend, t0 + a.nkb) - t0);
+  g.slot = (int)blockIdx.x - (int)bg_owner(t0, T, (int)gridDim.x);
+  return g;
+}
 
 __host__ __device__ inline uint32_t bg_stage_bytes(int BN) {
   const uint32_t raw = (uint32_t)BG_PLANES * (BG_BM + BN) * BG_SW;
   return (raw + 1023u) / 1024u * 1024u;
 }
 
-// Persistent: CTA c takes work units c, c + grid, ... in order.  A unit is
-// (M-tile, N-tile, K-chunk).  Its K blocks are taken BG_DRAIN at a time (a
-// period): the MMAs of a period accumulate in one of BG_NBUF TMEM buffer
-// pairs (main product, corrections), which the epilogue then adds into the
-// unit's FP32 sums in registers while the MMAs fill the next pair.
+// Persistent: CTA c takes its contiguous range of (tile, K block) iterations
+// (bgemm.cuh), one piece per tile it meets.  The K blocks of a piece are
+// taken BG_DRAIN at a time (a period): the MMAs of a period accumulate in one
+// of BG_NBUF TMEM buffer pairs (main product, corrections), which the
+// epilogue then adds into the piece's FP32 sums in registers while the MMAs
+// fill the next pair.
 //   warp 0 lane 0: TMA producer (A and B planes of one K block per stage)
 //   warp 1:        TMEM allocation; lane 0 issues the MMAs and commits
 //   warps 2..9:    epilogue; warp w reads TMEM lanes 32 (w mod 4) .. +31 and
@@ -68,16 +79,18 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
-  const int U = a.MT * a.NT * a.KC;
+  const int64_t T = (int64_t)a.MT * a.NT * a.nkb;
+  const int64_t ibeg = (int64_t)blockIdx.x * T / gridDim.x, iend = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------ TMA producer
       int it = 0;
-      for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x) {
-        const int nt = u % a.NT, t = u / a.NT, kc = t % a.KC, mt = t / a.KC;
-        const int kb0 = kc * a.kc_blocks, kb1 = min(a.nkb, kb0 + a.kc_blocks);
-        for (int kb = kb0; kb < kb1; ++kb) {
+      for (int64_t i = ibeg; i < iend && !tmo;) {
+        const BGSeg g = bg_seg(a, i, iend, T);
+        i += g.kb1 - g.kb0;
+        const int nt = g.t % a.NT, mt = g.t / a.NT;
+        for (int kb = g.kb0; kb < g.kb1; ++kb) {
           const int s = it % S;
           if (it >= S && !mbar_wait<false>(&empty[s], ((it / S) - 1) & 1, a.limit_ns, a.status)) {
             tmo = 1;
@@ -100,10 +113,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
       const uint32_t idesc = umma_idesc_bf16(BG_BM, a.BN);
       const uint32_t sbase = smem_u32(smem);
       int it = 0, gp = 0;   // K blocks and drain periods issued by this CTA
-      for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x) {
-        const int t = u / a.NT, kc = t % a.KC;
-        const int kb0 = kc * a.kc_blocks, kb1 = min(a.nkb, kb0 + a.kc_blocks);
-        for (int pb = kb0; pb < kb1 && !tmo; pb += BG_DRAIN, ++gp) {
+      for (int64_t i = ibeg; i < iend && !tmo;) {
+        const BGSeg g = bg_seg(a, i, iend, T);
+        i += g.kb1 - g.kb0;
+        const int kb1 = g.kb1;
+        for (int pb = g.kb0; pb < kb1 && !tmo; pb += BG_DRAIN, ++gp) {
           const int b = gp % BG_NBUF;
           if (gp >= BG_NBUF && !mbar_wait<false>(&tempty[b], ((gp / BG_NBUF) - 1) & 1, a.limit_ns, a.status)) {
             tmo = 1;
@@ -111,6 +125,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
           }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(2 * b * BG_MAXN);   // main; corrections at + BG_MAXN
+          const uint32_t e = d + BG_MAXN;
           uint32_t acc = 0;
           const int pe = min(kb1, pb + BG_DRAIN);
           for (int kb = pb; kb < pe; ++kb, ++it) {
@@ -123,14 +138,23 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
             const uint32_t sa = sbase + (uint32_t)s * sstride, sb = sa + a_bytes;
 #pragma unroll
             for (int ks = 0; ks < BG_SW / 32; ++ks) {     // 16 BF16 = 32 bytes of K per MMA
-#pragma unroll
-              for (int pr = 0; pr < 6; ++pr) {
-                const uint64_t ad = sdesc_kmajor<BG_SW>(sa + kPlaneA[pr] * a_plane + ks * 32);
-                const uint64_t bd = sdesc_kmajor<BG_SW>(sb + kPlaneB[pr] * b_plane + ks * 32);
-                // the main product in its own accumulator, the rest in the second
-                umma_bf16(pr == 0 ? d : d + BG_MAXN, ad, bd, idesc, pr == 0 ? (acc & 1u) : (acc >> 1));
-                acc |= pr == 0 ? 1u : 2u;
-              }
+              // (plane of A, plane of B) of the six products kept, of
+              // significance 2^0, 2^-8 (twice), 2^-16 (three times; the
+              // dropped ones are below 2^-23 relative), grouped by the plane
+              // of A so that each A plane is read from shared memory once:
+              // the main product in its own accumulator, the rest in the second
+              const uint32_t oa = sa + ks * 32, ob = sb + ks * 32;
+              const uint64_t a0 = sdesc_kmajor<BG_SW>(oa), a1 = sdesc_kmajor<BG_SW>(oa + a_plane),
+                             a2 = sdesc_kmajor<BG_SW>(oa + 2 * a_plane);
+              const uint64_t b0 = sdesc_kmajor<BG_SW>(ob), b1 = sdesc_kmajor<BG_SW>(ob + b_plane),
+                             b2 = sdesc_kmajor<BG_SW>(ob + 2 * b_plane);
+              umma_bf16_col<1>(d, a0, b0, idesc, acc & 1u);
+              umma_bf16_col<2>(e, a0, b1, idesc, acc >> 1);
+              umma_bf16_col<3>(e, a0, b2, idesc, 1u);
+              umma_bf16_col<1>(e, a1, b0, idesc, 1u);
+              umma_bf16_col<3>(e, a1, b1, idesc, 1u);
+              umma_bf16_col<0>(e, a2, b0, idesc, 1u);
+              acc = 3u;
             }
             umma_commit(&empty[s]);   // the stage is free once these MMAs have read it
           }
@@ -148,9 +172,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int c0 = ((warp - 2) >> 2) * 64;   // this warp's 64 columns of the tile
     int gp = 0;
-    for (int u = blockIdx.x; u < U && !tmo; u += gridDim.x) {
-      const int nt = u % a.NT, t = u / a.NT, kc = t % a.KC, mt = t / a.KC;
-      const int kb0 = kc * a.kc_blocks, kb1 = min(a.nkb, kb0 + a.kc_blocks);
+    for (int64_t i = ibeg; i < iend && !tmo;) {
+      const BGSeg g = bg_seg(a, i, iend, T);
+      i += g.kb1 - g.kb0;
+      const int nt = g.t % a.NT, mt = g.t / a.NT;
+      const int kb0 = g.kb0, kb1 = g.kb1;
       const int ncols = min(a.BN, a.N - nt * a.BN);
       const int mine = min(64, ncols - c0);   // columns of this warp (<= 0: none)
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -186,7 +212,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1) bgemm_kernel(const __grid_const
       }
       const int row = mt * BG_BM + q * 32 + lane;
       if (row < a.M) {
-        double* dst = a.P + ((size_t)kc * a.N + (size_t)nt * a.BN + c0) * a.M + row;
+        double* dst = a.P + ((size_t)g.slot * a.N + (size_t)nt * a.BN + c0) * a.M + row;
 #pragma unroll
         for (int j = 0; j < 64; ++j)
           if (j < mine) __stcg(dst + (size_t)j * a.M, (double)hi[j]);
@@ -285,8 +311,9 @@ __global__ void reduce_link_kernel(const BatchIo io) {
   const int64_t chunk = (int64_t)io.m * io.n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < io.n; i += (int64_t)gridDim.x * blockDim.x) {
     const double* src = io.P1 + (int64_t)s * io.n + i;
+    const int ns = bg_slots(io.s1, (int)(i / BG_BM) * io.s1.NT + s / io.s1.BN);
     double z = 0.0;
-    for (int kc = 0; kc < io.KC1; ++kc) z += __ldcg(src + kc * chunk);   // fixed order
+    for (int kc = 0; kc < ns; ++kc) z += __ldcg(src + kc * chunk);   // fixed order
     zout[i] = z;
     const double yd = io.y ? io.y[i] : 0.0;
     double r0, r1 = 0.0;
@@ -323,9 +350,11 @@ __global__ void reduce_grad_kernel(const BatchIo io) {
   for (int q = 0; q < io.NB; ++q) {
     const double* src = io.P2 + ((int64_t)q * io.m + s) * io.p;
     double* dst = io.part + ((int64_t)s * io.NB + q) * io.p;
+    const int nt = (q * io.m + s) / io.s2.BN;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < io.p; j += (int64_t)gridDim.x * blockDim.x) {
+      const int ns = bg_slots(io.s2, (int)(j / BG_BM) * io.s2.NT + nt);
       double g = 0.0;
-      for (int kc = 0; kc < io.KC2; ++kc) g += __ldcg(src + kc * chunk + j);
+      for (int kc = 0; kc < ns; ++kc) g += __ldcg(src + kc * chunk + j);
       dst[j] = g;
     }
   }
@@ -352,7 +381,7 @@ inline unsigned grid1(int64_t work, int block) {
 
 }  // namespace
 
-cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K, int kc) {
+cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K) {
   pl = BGPlan{};
   if (M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0, optin = 0;
@@ -367,16 +396,22 @@ cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K, int kc) {
   pl.MT = (M + BG_BM - 1) / BG_BM;
   pl.nkb = (K + BG_BK - 1) / BG_BK;
   const int tiles = pl.MT * pl.NT;
-  if (kc <= 0) kc = std::max(1, (3 * nsm + tiles - 1) / tiles);
-  kc = std::min(std::min(kc, BG_MAXKC), pl.nkb);
-  pl.kc_blocks = (pl.nkb + kc - 1) / kc;
-  pl.KC = (pl.nkb + pl.kc_blocks - 1) / pl.kc_blocks;
+  const int64_t T = (int64_t)tiles * pl.nkb;
+  // one range per SM; fewer when a tile would be cut into more than BG_MAXKC pieces
+  int G = (int)std::min<int64_t>({(int64_t)std::max(nsm, 1), T, (int64_t)(BG_MAXKC - 1) * tiles});
+  for (;; --G) {
+    pl.grid = G;
+    const BGSplit sp = pl.split();
+    int kc = 1;
+    for (int t = 0; t < tiles; ++t) kc = std::max(kc, bg_slots(sp, t));
+    pl.KC = kc;
+    if (kc <= BG_MAXKC || G == 1) break;
+  }
   const uint32_t sb = bg_stage_bytes(pl.BN);
   const int fixed = 1024 + 512;   // alignment slack, static shared memory
   pl.stages = std::min(BG_MAXS, (optin - fixed) / (int)sb);
   if (pl.stages < 2) return cudaErrorNotSupported;
   pl.smem = (size_t)pl.stages * sb + 1024;
-  pl.grid = std::min(pl.MT * pl.NT * pl.KC, nsm);
   cudaFuncAttributes fa{};
   cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&bgemm_kernel));
   if (e != cudaSuccess) return e;
@@ -406,7 +441,9 @@ cudaError_t bgemm_encode(CUtensorMap* tm, const void* planes, int64_t K, int64_t
 }
 
 cudaError_t bgemm_launch(const BGPlan& pl, const BGArgs& a, cudaStream_t st) {
-  if (a.BN != pl.BN || a.stages != pl.stages || a.KC != pl.KC || a.KC > BG_MAXKC) return cudaErrorInvalidValue;
+  if (a.BN != pl.BN || a.stages != pl.stages || a.NT != pl.NT || a.MT != pl.MT || a.nkb != pl.nkb ||
+      pl.KC > BG_MAXKC || pl.grid < 1)
+    return cudaErrorInvalidValue;
   bgemm_kernel<<<pl.grid, BG_THREADS, pl.smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -18,11 +18,14 @@
 // drain them into FP32 registers (round to nearest) while the MMAs fill the
 // other of two TMEM buffer pairs.
 //
-// The K range is also cut into chunks for parallelism; each work unit
-// (M-tile, N-tile, K-chunk) writes its partial tile in FP64 (hi + lo), and a
-// reduction kernel sums the chunks in FP64 in a fixed order (deterministic),
-// fused with what consumes the product: the link of the loss (Z = X B) or the
-// per-node gradient layout of the p-phase (G = X' R).
+// Schedule.  The iteration space (tile, K block), tiles in order with the
+// N-tiles innermost, is cut into one contiguous range per CTA of equal length
+// (to one K block), so every SM gets the same work whatever the tile count.
+// A range covers the end of one tile, whole tiles, the start of another; each
+// piece writes its partial tile in FP64 to slot (CTA - first CTA of the
+// tile), and a reduction kernel sums a tile's slots in FP64 in slot order
+// (deterministic), fused with what consumes the product: the link of the
+// loss (Z = X B) or the per-node gradient layout of the p-phase (G = X' R).
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -41,30 +44,52 @@ constexpr int BG_DRAIN = 4;         // K blocks accumulated in TMEM between drai
 constexpr int BG_PLANES = 3;
 constexpr int BG_MAXS = 8;          // pipeline stages at most
 constexpr int BG_THREADS = 320;     // producer warp, MMA warp, eight epilogue warps
-constexpr int BG_MAXKC = 16;        // K chunks at most (partials are KC x N x M doubles)
+constexpr int BG_MAXKC = 16;        // partial slots per tile at most (partials are KC x N x M doubles)
+
+// The split of the iteration space: MT x NT tiles of nkb K blocks over `grid`
+// CTAs; CTA c takes [c T / grid, (c + 1) T / grid), T = MT NT nkb.
+struct BGSplit {
+  int MT = 1, NT = 1, BN = 16, nkb = 1, grid = 1;
+};
+// the CTA whose range holds iteration i
+__host__ __device__ inline int64_t bg_owner(int64_t i, int64_t T, int grid) { return ((i + 1) * grid - 1) / T; }
+// first CTA of tile t and its number of slots (CTAs whose range meets the tile)
+__host__ __device__ inline int bg_first(const BGSplit& s, int t) {
+  const int64_t T = (int64_t)s.MT * s.NT * s.nkb;
+  return (int)bg_owner((int64_t)t * s.nkb, T, s.grid);
+}
+__host__ __device__ inline int bg_slots(const BGSplit& s, int t) {
+  const int64_t T = (int64_t)s.MT * s.NT * s.nkb;
+  return (int)(bg_owner((int64_t)(t + 1) * s.nkb - 1, T, s.grid) - bg_owner((int64_t)t * s.nkb, T, s.grid)) + 1;
+}
 
 struct BGArgs {
   CUtensorMap tmA;        // planes of A: dims {K, M, 3}, box {BG_BK, 128, 3}
   CUtensorMap tmB;        // planes of B: dims {K, N, 3}, box {BG_BK, BN, 3}
   int M, N, K;
-  int BN, NT, MT, KC;     // tile columns, N-tiles, M-tiles, K-chunks
-  int kc_blocks, nkb;     // K blocks (of BG_BK) per chunk, K blocks over K
+  int BN, NT, MT;         // tile columns, N-tiles, M-tiles
+  int nkb;                // K blocks (of BG_BK) over K
   int stages;
-  double* P;              // [KC][N][M] partial products (FP64)
+  double* P;              // [slot][N][M] partial products (FP64)
   int* status;
   uint64_t limit_ns;
 };
 
 struct BGPlan {
   int M = 0, N = 0, K = 0;
-  int BN = 16, NT = 1, MT = 1, KC = 1, kc_blocks = 1, nkb = 1, stages = 2, grid = 1;
+  int BN = 16, NT = 1, MT = 1, KC = 1, nkb = 1, stages = 2, grid = 1;   // KC: slots per tile at most
   size_t smem = 0;
+  BGSplit split() const {
+    BGSplit s;
+    s.MT = MT; s.NT = NT; s.BN = BN; s.nkb = nkb; s.grid = grid;
+    return s;
+  }
 };
 
 // Tile plan of D (M x N) = A B^T over K: BN and the N-tiles from N, the
-// stages from shared memory, and KC chunks of K (kc <= 0: about three work
-// units per SM).
-cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K, int kc);
+// stages from shared memory, one CTA per SM (fewer when the tiles' slots
+// would exceed BG_MAXKC or there are fewer K blocks than SMs).
+cudaError_t bgemm_plan(BGPlan& pl, int M, int N, int K);
 // Tensor map of three BF16 planes [3][rows][ld] with `rows` rows of K valid
 // elements (ld >= K, a multiple of 8), box {BG_BK, box_rows, 3}, 64-byte swizzle.
 cudaError_t bgemm_encode(CUtensorMap* tm, const void* planes, int64_t K, int64_t rows, int64_t ld,
@@ -91,10 +116,10 @@ struct BatchIo {
   const double* y;
   __nv_bfloat16* Bp;     // [3][nb][ldp] planes of the node points
   __nv_bfloat16* Rp;     // [3][NB nb][ldn] planes of the link (the second product's B)
-  const double* P1;      // [KC1][m][n] partials of Z = X B
-  int KC1;
-  const double* P2;      // [KC2][NB m][p] partials of G = X' R
-  int KC2;
+  const double* P1;      // [slot][m][n] partials of Z = X B
+  BGSplit s1;
+  const double* P2;      // [slot][NB m][p] partials of G = X' R
+  BGSplit s2;
   double* part;          // [m][NB][p] gradients per node (p-phase layout)
 };
 // B planes of the active nodes' next points

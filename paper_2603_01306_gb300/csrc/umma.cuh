@@ -41,6 +41,37 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same with a collector-buffer hint for A: consecutive MMAs that read the
+// same A tile keep it in the tensor core's collector instead of reading
+// shared memory again.  COL 1: read A and keep it (fill); 2: use the kept A
+// (use); 3: use it for the last time (lastuse); 0: no hint.  An MMA with hint
+// 2 or 3 must follow, in issue order, an MMA of the same A with hint 1 or 2.
+template <int COL>
+__device__ __forceinline__ void umma_bf16_col(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  static_assert(COL >= 0 && COL <= 3, "collector hint");
+  if constexpr (COL == 0) {
+    umma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+  } else if constexpr (COL == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else if constexpr (COL == 2) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
 // the mbarrier gets one arrival once every tcgen05 operation this thread has
 // issued so far has completed
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {

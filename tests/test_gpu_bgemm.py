@@ -10,7 +10,7 @@ element, relative to the sum of the magnitudes of its terms (|X| |b|):
   * typical: the RMS of that relative error <= 2e-7, which a product left
     out (x1 b3, ~2^-16 per term) or a plane laid out wrong would exceed.
 The shapes span several M, N and K tiles with ragged tails, one N-tile and
-two, and N = 1.  FP64 X uses FP64 products (1e-12 relative)."""
+two, N = 1, and a long K over few tiles (a tile summed from 16 pieces).  FP64 X uses FP64 products (1e-12 relative)."""
 import numpy as np
 import pytest
 
@@ -28,6 +28,7 @@ SHAPES = [
     (130, 64, 1),
     (700, 1500, 300),     # two N tiles (balanced: 2 x 160)
     (4000, 3000, 64),
+    (200, 20000, 8),      # 2 tiles of 625 K blocks: each cut into 15-16 pieces of the CTAs' ranges
 ]
 
 
@@ -68,7 +69,7 @@ def test_batch_products_f32_match_fp64(lib, shape):
     g_ref = z @ X64
     rg = _check(g, g_ref, np.abs(z) @ np.abs(X64), n)
     print(f"shape {shape}: RMS relative error z {rz:.2e}, g {rg:.2e}")
-    # deterministic: fixed chunking and fixed-order FP64 sums
+    # deterministic: a fixed split and fixed-order FP64 sums
     z2, g2 = h.batch_xpass(torch.tensor(B, device="cuda"))
     assert np.array_equal(z2.cpu().numpy(), z) and np.array_equal(g2.cpu().numpy(), g)
     h.close()
