@@ -780,7 +780,10 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       std::fprintf(stderr, "[relax] loop pass: xk=%d Gc=%d Gr=%d sw=%lld (%d x %d) B=%d nblk=%d SA=%d SB=%d lag=%d threads=%d smem=%zu\n",
                    q.xk, q.Gc, q.Gr, (long long)q.sw, q.nbox, q.inner, q.B, q.nblk, q.SA, q.SB, q.lag, q.threads, q.smem);
     }
-    TRYC(pphase_plan(h->pp_iter, true, p, h->backtrack != 0));
+    // FP32, BF16 and FP8 data: the loop's per-coordinate arithmetic in FP32
+    // (FP64 at a small fraction of the FP32 rate on this GPU); FP64 data keeps
+    // FP64 throughout
+    TRYC(pphase_plan(h->pp_iter, true, p, h->backtrack != 0, h->xk_loop != XK_F64 && !h->backtrack));
     TRYC(pphase_plan(h->pp_eval, true, p));
     {
       const XSPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
@@ -1483,7 +1486,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   // fewest CTAs that cover p in cooperative waves of co-resident segments
   PPlan pp = h->pp_iter;
   PPlan pc;
-  const bool clustered = pphase_cluster_plan(pc, p, h->backtrack != 0) == cudaSuccess && !std::getenv("RELAX_BATCH_WAVES");
+  const bool clustered = pphase_cluster_plan(pc, p, h->backtrack != 0, !f64 && !h->backtrack) == cudaSuccess &&
+                         !std::getenv("RELAX_BATCH_WAVES");
   cudaGetLastError();   // a refused cluster plan leaves no sticky error
   const int segb = clustered ? pc.seg
                              : (int)std::max<int64_t>(1, (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT));

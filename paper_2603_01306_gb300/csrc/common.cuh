@@ -8,7 +8,7 @@
 
 namespace relax {
 
-enum : int { ST_OK = 0, ST_TIMEOUT = 5, ST_NUMERIC = 6 };
+enum : int { ST_OK = 0, ST_TIMEOUT = 5, ST_NUMERIC = 6, ST_INTERNAL = 7 };   // ST_INTERNAL: a kernel launched outside its plan (reported as RELAX_ECUDA)
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
@@ -127,6 +127,17 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_cluster_u64(uint32_t addr) {
+  unsigned long long v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 // consumer-only named barrier (id 1), `nthreads` a multiple of 32
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -142,8 +153,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
   __syncthreads();
   __shared__ int ok_sh;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1ull);
+    // release at GPU scope: the block's writes before the __syncthreads are
+    // visible to every block that acquires the counter's final value
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(counter) : "memory");
     int ok = 1;
     unsigned long long v;
     asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(counter) : "memory");

@@ -45,8 +45,9 @@ struct PPlan {
   bool vdouble = false;
   int seg = 0;             // cluster plans: CTAs per problem (the cluster size)
 };
-// backtrack: the instantiation with the backtracking step rule (FP64 vectors)
-cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack = false);
+// backtrack: the instantiation with the backtracking step rule (FP64 vectors);
+// fast: the loop's FP32 per-coordinate instantiation (FP32 data, fixed step)
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack = false, bool fast = false);
 cudaError_t pphase_launch(const PPlan& pl, const PArgs& a, cudaStream_t st);
 // the same kernel on `grid` CTAs (a segmented launch: grid = segments x a.seg_blocks <= maxgrid)
 cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaStream_t st);
@@ -54,7 +55,9 @@ cudaError_t pphase_launch_grid(const PPlan& pl, const PArgs& a, int grid, cudaSt
 // cluster of pl.seg CTAs: PEPT coordinates per thread on up to 16 CTAs where
 // the device allows that non-portable cluster size, else PEPT_CLUSTER on up to
 // 8; cudaErrorNotSupported when p needs more.
-cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p, bool backtrack = false);
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p, bool backtrack = false, bool fast = false);
+// the cluster instantiation with `ept` coordinates per thread (PEPT or PEPT_CLUSTER)
+const void* pphase_cluster_kernel(int ept, bool backtrack, bool fast);
 // nseg clusters (a.seg_blocks = pl.seg, a.cluster = 1); no co-residency needed
 cudaError_t pphase_launch_clusters(const PPlan& pl, const PArgs& a, int nseg, cudaStream_t st);
 

@@ -5,11 +5,13 @@
 
 namespace relax {
 
-cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack) {
+cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack, bool fast) {
   pl = PPlan{};
   pl.vdouble = vdouble;
   if (backtrack && !vdouble) return cudaErrorNotSupported;   // the loop's vectors are FP64
+  if (fast && (backtrack || !vdouble)) return cudaErrorNotSupported;
   pl.kernel = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT, true>)
+              : fast    ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT, false, false, true>)
               : vdouble ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>)
                         : reinterpret_cast<const void*>(&pphase_kernel<float, PEPT>);
   int dev = 0, nsm = 0, per = 0;
@@ -86,11 +88,10 @@ static cudaError_t cluster_try(PPlan& pl, int64_t p, const void* kernel, int ept
   return cudaSuccess;
 }
 
-cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p, bool backtrack) {
-  const void* k4 = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT, true>)
-                             : reinterpret_cast<const void*>(&pphase_kernel<double, PEPT>);
-  const void* k8 = backtrack ? reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER, true>)
-                             : reinterpret_cast<const void*>(&pphase_kernel<double, PEPT_CLUSTER>);
+cudaError_t pphase_cluster_plan(PPlan& pl, int64_t p, bool backtrack, bool fast) {
+  if (fast && backtrack) return cudaErrorNotSupported;
+  const void* k4 = pphase_cluster_kernel(PEPT, backtrack, fast);
+  const void* k8 = pphase_cluster_kernel(PEPT_CLUSTER, backtrack, fast);
   if (cluster_try(pl, p, k4, PEPT, 16) == cudaSuccess) return cudaSuccess;
   return cluster_try(pl, p, k8, PEPT_CLUSTER, 8);
 }

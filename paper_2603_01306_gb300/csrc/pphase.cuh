@@ -34,6 +34,8 @@
 // z-sums in 32.32 fixed point), so every block takes identical decisions; FP64
 // sums go through per-block partials summed in a fixed order (deterministic).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "xpass.cuh"
 
@@ -166,6 +168,43 @@ __device__ __forceinline__ KT warm_cand(KT kc, KT lo, KT hi, int q, int shift) {
   return (KT)x;
 }
 
+// Float-float sums (Knuth's TwoSum; about 48 significant bits from FP32
+// instructions).  This GPU issues FP64 arithmetic, comparisons and
+// conversions at about 1.6 lanes per clock per SM against about 112 for FP32
+// (measured), so the loop's per-coordinate work on FP32 data (the FAST
+// instantiation) is FP32 with float-float sums.
+struct ffs {
+  float hi, lo;
+};
+// s += x
+__device__ __forceinline__ void ff_acc(ffs& s, float x) {
+  const float t = s.hi + x;
+  const float bp = t - s.hi;
+  s.lo += (s.hi - (t - bp)) + (x - bp);
+  s.hi = t;
+}
+// s += x for an FP64 x (split into two floats first)
+__device__ __forceinline__ void ff_acc(ffs& s, double x) {
+  const float h = (float)x;
+  ff_acc(s, h);
+  s.lo += (float)(x - (double)h);
+}
+// a + b, renormalised; symmetric in a and b (every lane of a butterfly gets
+// the same bits)
+__device__ __forceinline__ ffs ff_add(ffs a, ffs b) {
+  const float t = a.hi + b.hi;
+  const float bp = t - a.hi;
+  const float e = (a.hi - (t - bp)) + (b.hi - bp);
+  const float lo = e + (a.lo + b.lo);
+  const float h = t + lo;
+  return ffs{h, lo - (h - t)};
+}
+__device__ __forceinline__ ffs ff_of(double x) {
+  const float h = (float)x;
+  return ffs{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
 __device__ __forceinline__ unsigned long long fixp(float z) {
   return __float2ull_rz(z * 4294967296.0f);
 }
@@ -185,10 +224,17 @@ __device__ __forceinline__ void cluster_barrier() {
 // float or double for the standalone entry points).  EPT: elements per thread
 // (at most), so one CTA covers PBLOCK * EPT coordinates.  BT: the backtracking
 // step rule is compiled in (its test and retry cost registers that the
-// fixed-step loop does not pay).
-template <typename TV, int EPT = PEPT, bool BT = false>
+// fixed-step loop does not pay).  CL: the cluster-per-problem launch, whose
+// sums go through distributed shared memory.  FAST (the loop on FP32 data,
+// PM_ITER only): the per-coordinate arithmetic in FP32 with float-float
+// sums; FP64 only where beta^t or beta^{t-1} is nonzero (the iterate's FP64
+// accumulation), for the prox outputs that are nonzero, and per row of the
+// loss.  Every threshold decision stays exact for the values it classifies.
+template <typename TV, int EPT = PEPT, bool BT = false, bool CL = false, bool FAST = false>
 __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
-  using KG = unsigned long long;   // S1 keys: FP32 or FP64 bit patterns of |a|
+  static_assert(!FAST || (sizeof(TV) == 8 && !BT), "FAST: FP64 iterates, fixed step");
+  // S1 keys: FP32 or FP64 bit patterns of |a|
+  using KG = typename std::conditional<FAST, uint32_t, unsigned long long>::type;
   using KV = uint32_t;             // FP32 keys of the S2 / S3 thresholds
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this CTA's problem: the whole grid, or its segment of a batched launch
@@ -215,17 +261,29 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   __shared__ double red_d[PNW][NBP];
   __shared__ double sh_tot[NBP];
   __shared__ int sh_done;
+  // cluster launches: this CTA's partial of each grid-wide sum, read by the
+  // cluster's CTAs from distributed shared memory (two buffers, alternating:
+  // a buffer is rewritten only after the next barrier, which every CTA
+  // reaches after its reads of the previous use)
+  __shared__ unsigned long long cl_u[2][NFIELD * PQ];
+  __shared__ double cl_d[2][NBP];
+  __shared__ float2 red_f[PNW][NBP];
+  __shared__ float2 cl_f[2][NBP];
 
   if (tid == 0) sh_done = (st != nullptr) ? st->done : 0;
   __syncthreads();
   if (sh_done) return;   // uniform: every block reads the same flag
+  if (FAST && (a_in.mode != PM_ITER || st == nullptr)) {   // the host plans FAST for the loop only
+    if (blockIdx.x == 0 && tid == 0) atomicCAS(a_in.status, ST_OK, ST_INTERNAL);
+    return;
+  }
 
   const unsigned long long bar0 = st ? st->bar_base : a.bar_base;
   int nbar = 0;
   bool alive = true;
   auto barrier = [&]() {
     ++nbar;
-    if (a_in.cluster) {
+    if (CL) {
       cluster_barrier();
       return;
     }
@@ -233,9 +291,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       alive = false;
   };
   int nstep = 0;
-  // grid-wide deterministic FP64 sum of NV values
+  // grid-wide deterministic FP64 sum of NV values: block partials summed by
+  // lane (block b on lane b mod 32) and a warp butterfly, the same order for
+  // the global-memory partials of a cooperative grid and the distributed
+  // shared memory of a cluster
   auto gsum = [&](double* v, int nv) {
-    double* bp = a.bpart + (size_t)(nstep & 1) * nbk * NBP;
+    const int buf = nstep & 1;
+    double* bp = CL ? nullptr : a.bpart + (size_t)buf * nbk * NBP;
     ++nstep;
     for (int i = 0; i < nv; ++i) {
       double s = warp_sum(v[i]);
@@ -245,12 +307,17 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (tid < nv) {
       double s = 0.0;
       for (int w = 0; w < PNW; ++w) s += red_d[w][tid];
-      bp[(size_t)lbk * NBP + tid] = s;
+      if (CL) cl_d[buf][tid] = s;
+      else bp[(size_t)lbk * NBP + tid] = s;
     }
     barrier();
     for (int c = warp; c < nv; c += PNW) {
       double s = 0.0;
-      for (int b = lane; b < nbk; b += 32) s += __ldcg(bp + (size_t)b * NBP + c);
+      if (CL) {
+        if (lane < nbk) s = ld_cluster_f64(mapa(&cl_d[buf][c], (uint32_t)lane));
+      } else {
+        for (int b = lane; b < nbk; b += 32) s += __ldcg(bp + (size_t)b * NBP + c);
+      }
       s = warp_sum(s);
       if (lane == 0) sh_tot[c] = s;
     }
@@ -258,9 +325,60 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     for (int i = 0; i < nv; ++i) v[i] = sh_tot[i];
     __syncthreads();
   };
+  // the same over float-float partials (FAST): a warp butterfly, the warps in
+  // order, the blocks' partials (two floats each) by lane and a butterfly;
+  // the totals in FP64
+  auto gsum_ff = [&](ffs* v, int nv, double* out) {
+    const int buf = nstep & 1;
+    float2* bp = CL ? nullptr : reinterpret_cast<float2*>(a.bpart + (size_t)buf * nbk * NBP);
+    ++nstep;
+    for (int i = 0; i < nv; ++i) {
+      ffs s = v[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const ffs t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = ff_add(s, t);
+      }
+      if (lane == 0) red_f[warp][i] = make_float2(s.hi, s.lo);
+    }
+    __syncthreads();
+    if (tid < nv) {
+      ffs s{red_f[0][tid].x, red_f[0][tid].y};
+      for (int w = 1; w < PNW; ++w) s = ff_add(s, ffs{red_f[w][tid].x, red_f[w][tid].y});
+      if (CL) cl_f[buf][tid] = make_float2(s.hi, s.lo);
+      else bp[(size_t)lbk * NBP + tid] = make_float2(s.hi, s.lo);
+    }
+    barrier();
+    for (int c = warp; c < nv; c += PNW) {
+      ffs s{0.f, 0.f};
+      if (CL) {
+        if (lane < nbk) {
+          const uint32_t ra = mapa(&cl_f[buf][c], (uint32_t)lane);
+          float hi, lo;
+          asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(hi), "=f"(lo) : "r"(ra) : "memory");
+          s = ffs{hi, lo};
+        }
+      } else {
+        for (int b = lane; b < nbk; b += 32) {
+          const float2 q = __ldcg(bp + (size_t)b * NBP + c);
+          s = ff_add(s, ffs{q.x, q.y});
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const ffs t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = ff_add(s, t);
+      }
+      if (lane == 0) sh_tot[c] = (double)s.hi + (double)s.lo;
+    }
+    __syncthreads();
+    for (int i = 0; i < nv; ++i) out[i] = sh_tot[i];
+    __syncthreads();
+  };
   int nround = 0;
   // publish per-lane round fields (lane = candidate) and fetch the grid totals
   auto round_reduce = [&](unsigned long long (&f)[NFIELD], int nf) {
+    const int buf = nround & 1;
     unsigned long long* accb = a.acc + (size_t)(nround % 3) * ACC_STRIDE;
     unsigned long long* accz = a.acc + (size_t)((nround + 1) % 3) * ACC_STRIDE;
     ++nround;
@@ -269,12 +387,27 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     for (int t = tid; t < nf * PQ; t += PBLOCK) {
       unsigned long long s = 0;
       for (int w = 0; w < PNW; ++w) s += red_u[w][t];
-      if (s) atomicAdd(accb + t, s);
+      if (CL) cl_u[buf][t] = s;
+      else if (s) atomicAdd(accb + t, s);
     }
-    if (lbk == 0)
+    if (!CL && lbk == 0)
       for (int t = tid; t < ACC_STRIDE; t += PBLOCK) accz[t] = 0ull;
     barrier();
-    for (int t = tid; t < nf * PQ; t += PBLOCK) sh_acc[t] = __ldcg(accb + t);
+    if (CL) {
+      for (int t = tid; t < nf * PQ; t += PBLOCK) {
+        const uint32_t loc = smem_u32(&cl_u[buf][t]);
+        unsigned long long s = 0;
+#pragma unroll 4
+        for (int r = 0; r < nbk; ++r) {
+          uint32_t ra;
+          asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(loc), "r"(r));
+          s += ld_cluster_u64(ra);
+        }
+        sh_acc[t] = s;
+      }
+    } else {
+      for (int t = tid; t < nf * PQ; t += PBLOCK) sh_acc[t] = __ldcg(accb + t);
+    }
     __syncthreads();
   };
 
@@ -306,7 +439,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
   const double* part = static_cast<const double*>(a.part);
   // S1 keys: FP64 patterns when the values are FP64 and exactness is asked for
-  const bool key64 = !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
+  const bool key64 = !FAST && !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
+  // FAST: the FP32 forms of the scalars
+  const double inv2l = 1.0 / (2.0 * lam2);
+  const double Mtol = M * (1.0 + 1e-6);
+  const float M32 = (float)M;
+  const float inv2l32 = (float)inv2l;
 
   int8_t fx[EPT];
   KG ka[EPT];        // S1 keys: |a| on Jf, 0 elsewhere
@@ -349,6 +487,63 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
   const bool need_a = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GSTAR);
   const bool need_b = (mode == PM_ITER || mode == PM_EVAL || mode == PM_GVAL);
+  float gf[EPT];     // FAST: G^t in FP32
+  float gyf[EPT];    // FAST: the logistic second gradient in FP32
+  ffs sf[NBP];       // FAST: the sums s0 as float-float
+  if constexpr (FAST) {
+    // The bulk of the coordinates (beta^t_j = 0, not fixed) costs FP32 work
+    // only; the terms of Phi and Psi that are not zero there (fixed-in
+    // coordinates, nonzero beta^t_j, and the whole free set when the
+    // cardinality budget is slack) are FP64, as are their sums (float-float).
+    int c_nnz = 0, c_dom = 0, c_bad = 0;
+    const bool slack = st->pbar <= st->kbar;   // TopSum = sum over the free set of H(|a|)
+#pragma unroll
+    for (int i = 0; i < NBP; ++i) sf[i] = ffs{0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+      fx[e] = 0; ka[e] = 0; bmf[e] = 0.f; bt[e] = (TV)0; gf[e] = 0.f; gyf[e] = 0.f;
+      if (j >= p) { fx[e] = -2; continue; }
+      const int8_t f = a.fix ? a.fix[j] : (int8_t)0;
+      fx[e] = f;
+      double G = 0.0, Gy = 0.0;   // partials summed in FP64, fixed order
+      for (int c = 0; c < a.ncl; ++c) {
+        G += part[((int64_t)c * a.NB) * p + j];
+        if (a.NB > 1) Gy += part[((int64_t)c * a.NB + 1) * p + j];
+      }
+      Gcur[j] = G;
+      gf[e] = (float)G;
+      if (a.NB > 1) gyf[e] = (float)Gy;
+      const float aa = fabsf(gf[e]) * inv2l32;   // |a_j| in FP32 (keys), a = -G / (2 lambda2)
+      if (!isfinite(aa)) ++c_bad;
+      if (f > 0) ff_acc(sf[0], huber_d<double>(fabs(G) * inv2l, M));
+      if (f == 0) {
+        ka[e] = key_of(aa);
+        if (slack) ff_acc(sf[7], huber_d<double>(fabs(G) * inv2l, M));
+      }
+      const TV b = bcur[j];
+      bt[e] = b;
+      if (!is_zero_bits((double)b)) {          // most coordinates of beta^t are zero
+        const double bd = (double)b;
+        const double ab = fabs(bd);
+        if (!isfinite(bd)) ++c_bad;
+        if (f > 0) { ff_acc(sf[1], bd * bd); if (ab > Mtol) ++c_dom; }
+        else if (f < 0) ++c_dom;
+        else {
+          bmf[e] = (float)ab;
+          ff_acc(sf[2], ab);
+          ff_acc(sf[3], ab * ab);
+          ++c_nnz;
+          if (ab > Mtol) ++c_dom;
+        }
+      }
+    }
+    sf[4] = ffs{(float)c_nnz, 0.f};
+    sf[5] = ffs{(float)c_dom, 0.f};
+    sf[6] = ffs{(float)c_bad, 0.f};
+    sf[8] = ff_of(s0[8]);
+    sf[9] = ff_of(s0[9]);
+  } else {
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int64_t j = (int64_t)gt + (int64_t)e * nthr;
@@ -396,6 +591,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
     }
   }
+  }
   const int kbar = st ? st->kbar : 0;   // filled below for the standalone modes
   int kb = kbar, pb = st ? st->pbar : 0;
   double tot[NBP];
@@ -408,7 +604,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       if (fx[e] == 0) cnt2[1] += 1.0;
     }
   }
-  gsum(tot, NBP);
+  if constexpr (FAST) gsum_ff(sf, NBP, tot);
+  else gsum(tot, NBP);
   if (!st) {
     gsum(cnt2, 2);
     kb = a.k - (int)cnt2[0];
@@ -440,7 +637,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   double topsum = 0.0, gval = 0.0;
   KG lo1 = 0, hi1 = key64 ? (KG)(KeyOf<double>::kInf + 1) : (KG)(KeyOf<float>::kInf + 1);
   KV lo2 = 0, hi2 = (KV)KeyOf<float>::kInf;
-  double c2lo = 0.0, c2hi = 0.0;   // #{|b| > lo2}, #{|b| > hi2}
+  unsigned long long c2lo = 0, c2hi = 0;   // #{|b| > lo2}, #{|b| > hi2}
   if (need_a) {
     if (kb <= 0) topsum = 0.0;
     else if (pb <= kb) topsum = tot[7];
@@ -463,7 +660,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (g_inf) gval = INFINITY;
     else if (kb <= 0) gval = 0.5 * tot[1];
     else if (tot[4] <= (double)kb) gval = 0.5 * (tot[1] + tot[3]);
-    else if (!w_known) { s2 = true; c2lo = tot[4]; c2hi = 0.0; }
+    else if (!w_known) { s2 = true; c2lo = (unsigned long long)tot[4]; c2hi = 0; }
   }
 
   // ------------------------------------------------------- S1 / S2 rounds
@@ -528,11 +725,11 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
     if (s2) {
       KV nlo = lo2, nhi = hi2;
-      double nclo = c2lo, nchi = c2hi;
+      unsigned long long nclo = c2lo, nchi = c2hi;
       const unsigned long long thr = (unsigned long long)kb << 32;
       for (int q = 0; q < PQ; ++q) {
         const KV xq = cand2(q);
-        const double cq = (double)sh_acc[F_S2C * PQ + q];
+        const unsigned long long cq = sh_acc[F_S2C * PQ + q];
         if (sh_acc[F_S2Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nclo = cq; } }
         else if (xq < nhi) { nhi = xq; nchi = cq; }
       }
@@ -558,6 +755,33 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   bool first = true;
   while (first || pol2) {
     double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if constexpr (FAST) {
+      // only the coordinates at or above t* (FP32 keys: the others have
+      // |a_j| < t*) and the nonzero |beta_j| contribute: FP64 for those
+      ffs vf[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      int nab = 0;
+      if (first && fin1) {
+        for (int e = 0; e < EPT; ++e) {
+          if (fx[e] != 0 || ka[e] < (KG)lo1) continue;
+          const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+          const double hv = huber_d<double>(fabs(Gcur[j]) * inv2l, M) - htstar;
+          if (hv > 0.0) ff_acc(vf[0], hv);
+        }
+      }
+      if (pol2) {
+        for (int e = 0; e < EPT; ++e) {
+          if (!(bmf[e] > 0.f)) continue;
+          const double m = fabs((double)bt[e]);
+          if (m > wcur) {
+            ++nab;
+            ff_acc(vf[3], m);
+            ff_acc(vf[4], m * m);
+          }
+        }
+      }
+      vf[2] = ffs{(float)nab, 0.f};
+      gsum_ff(vf, 5, v);
+    } else {
     if (first && fin1) {
       const TV* av_src = mode == PM_GSTAR ? static_cast<const TV*>(a.vin) : nullptr;
       for (int e = 0; e < EPT; ++e) {
@@ -578,6 +802,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
     }
     gsum(v, 5);
+    }
     if (first && fin1) topsum = (double)kb * htstar + v[0];
     first = false;
     if (pol2) {
@@ -723,7 +948,54 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   float ti[EPT];   // T^{-1}(|v|) in FP32: where coordinate j reaches z_j = 1
   double nzv = 0.0;
   double nbad = 0.0;   // standalone prox: non-finite inputs (the output is then all NaN)
-  if (do_prox) {
+  // FAST: bit e of `wide` set when v_j is FP64 (vv[e]: beta^t_j or
+  // beta^{t-1}_j nonzero, or j fixed in the support); otherwise v_j is the
+  // FP32 value -s gy_j with |v_j| = mmf[e] and its sign in bit e of `negm`
+  unsigned wide = 0, negm = 0;
+  if (do_prox && FAST) {
+    // v_j = y_j - s gy_j: FP64 where beta^t_j or beta^{t-1}_j is nonzero (or
+    // j is fixed in), FP32 elsewhere, where y_j = 0
+    const float mu32 = (float)mu, s32 = (float)step, opm32 = (float)(1.0 + mu);
+    const float M1r32 = (float)(M * (1.0 + rho)), rr32 = (float)(rho / (1.0 + rho));
+    int c_nz = 0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+      vv[e] = (TV)0; mmf[e] = 0.f; ti[e] = 0.f;
+      if (j >= p) continue;
+      const double b = (double)bt[e];
+      const double bp = (double)bprev[j];
+      float v32;
+      if (fx[e] > 0 || !is_zero_bits(b) || !is_zero_bits(bp)) {
+        double gyv;
+        if (a.loss == 0) {
+          gyv = mu == 0.0 ? Gcur[j] : (1.0 + mu) * Gcur[j] - mu * Gprev[j];
+        } else if (mu == 0.0) {
+          gyv = Gcur[j];
+        } else {
+          gyv = 0.0;
+          for (int c = 0; c < a.ncl; ++c) gyv += part[((int64_t)c * a.NB + 1) * p + j];
+        }
+        const double v = (b + mu * (b - bp)) - step * gyv;   // the iterate's FP64 accumulation
+        vv[e] = v;
+        v32 = (float)v;
+        wide |= 1u << e;
+      } else {
+        float gyv;
+        if (a.loss == 0) gyv = mu == 0.0 ? gf[e] : opm32 * gf[e] - mu32 * (float)Gprev[j];
+        else gyv = mu == 0.0 ? gf[e] : gyf[e];
+        v32 = -(s32 * gyv);
+      }
+      if (v32 < 0.f) negm |= 1u << e;
+      if (fx[e] == 0) {
+        const float m = fabsf(v32);
+        mmf[e] = m;
+        ti[e] = m <= M1r32 ? m * rr32 : m - M32;
+        if (m > 0.f) ++c_nz;
+      }
+    }
+    nzv = (double)c_nz;
+  } else if (do_prox) {
     const TV* vin = static_cast<const TV*>(a.vin);
     const TV muv = (TV)mu;
     const TV sv = (TV)step;
@@ -775,13 +1047,20 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (do_prox) {
     {
       double nv[2] = {nzv, nbad};
-      gsum(nv, 2);
+      if constexpr (FAST) {
+        ffs t[2] = {{(float)nzv, 0.f}, {0.f, 0.f}};
+        gsum_ff(t, 2, nv);
+      } else {
+        gsum(nv, 2);
+      }
       nzv = nv[0];
       nbad = nv[1];
     }
+    const float inv_rho32 = (float)(1.0 / rho);
     bool s3 = false;
     KV lo3 = 0, hi3 = (KV)KeyOf<float>::kInf;
-    double cmlo = nzv, cmhi = 0.0, ctlo = nzv, cthi = 0.0;   // #{m > lo}, #{m > hi}, same for T^-1
+    // #{m > lo}, #{m > hi}, the same for T^-1
+    unsigned long long cmlo = (unsigned long long)nzv, cmhi = 0, ctlo = (unsigned long long)nzv, cthi = 0;
     if (kb <= 0) c = INFINITY;
     else if (nzv <= (double)kb || nbad > 0.0) c = 0.0;   // no threshold search on a non-finite input
     else s3 = true;
@@ -794,9 +1073,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
       const KV x3 = cand3(lane);
       const float cq = from_key(x3, 0.f);
-      const double cqd = (double)cq;
-      const double wq = fmin(cqd / rho, M);
-      const float invw = (float)(1.0 / wq);
+      const float wq = fminf(cq * inv_rho32, M32);   // bracketing only: FP32
+      const float invw = 1.0f / wq;
       // |v_j| at or below the round's smallest candidate adds nothing for any
       // lane (and T^-1(|v_j|) <= |v_j| neither): only the coordinates above
       // it are broadcast, which after the first round are about the top kbar
@@ -821,11 +1099,11 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       // fields 3..5 live at indices F_S3Z.. ; reduce fields 0..5 (0..2 unused here)
       round_reduce(fld, 6);
       KV nlo = lo3, nhi = hi3;
-      double nmlo = cmlo, nmhi = cmhi, ntlo = ctlo, nthi = cthi;
+      unsigned long long nmlo = cmlo, nmhi = cmhi, ntlo = ctlo, nthi = cthi;
       const unsigned long long thr = (unsigned long long)kb << 32;
       for (int q = 0; q < PQ; ++q) {
         const KV xq = cand3(q);
-        const double cm = (double)sh_acc[F_S3CM * PQ + q], ct = (double)sh_acc[F_S3CT * PQ + q];
+        const unsigned long long cm = sh_acc[F_S3CM * PQ + q], ct = sh_acc[F_S3CT * PQ + q];
         if (sh_acc[F_S3Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nmlo = cm; ntlo = ct; } }
         else if (xq < nhi) { nhi = xq; nmhi = cm; nthi = ct; }
       }
@@ -843,6 +1121,27 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       for (int it = 0; it <= MAX_POLISH; ++it) {
         const double Tc = (ccur <= rhoM) ? ccur * (1.0 + rho) / rho : ccur + M;
         double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if constexpr (FAST) {
+          // an FP32 m satisfies m >= Tc iff m >= Tc rounded up, m > ccur iff
+          // m > ccur rounded down: exact classification in FP32
+          const float tcu = __double2float_ru(Tc), ccd = __double2float_rd(ccur);
+          int ntop = 0, nmid = 0;
+          ffs sm{0.f, 0.f};
+          for (int e = 0; e < EPT; ++e) {
+            if (fx[e] != 0) continue;
+            if (wide >> e & 1u) {
+              const double m = fabs((double)vv[e]);
+              if (m >= Tc) ++ntop;
+              else if (m > ccur) { ++nmid; ff_acc(sm, m); }
+            } else {
+              const float m = mmf[e];
+              if (m >= tcu) ++ntop;
+              else if (m > ccd) { ++nmid; ff_acc(sm, m); }
+            }
+          }
+          ffs t[3] = {{(float)ntop, 0.f}, {(float)nmid, 0.f}, sm};
+          gsum_ff(t, 3, v);
+        } else {
         for (int e = 0; e < EPT; ++e) {
           if (fx[e] != 0) continue;
           const double m = (double)mm[e];
@@ -850,6 +1149,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
           else if (m > ccur) { v[1] += 1.0; v[2] += m; }
         }
         gsum(v, 3);
+        }
         const double Ntop = v[0], Nmid = v[1], Smid = v[2];
         double cn;
         if (Nmid == 0.0) cn = ccur;   // flat piece: any c on it is a root when Ntop == kbar
@@ -877,6 +1177,36 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     double tst[2] = {0.0, 0.0};   // backtracking: <grad F(y), x - y>, ||x - y||^2
     const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
     double cnt[2] = {0, 0};
+    if constexpr (FAST) {
+      // FP64 only for the outputs that are nonzero (about the support)
+      const double inv1r = 1.0 / (1.0 + rho);
+      const float ccd = __double2float_rd(c);   // an FP32 m exceeds c iff it exceeds ccd
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+        if (j >= p) continue;
+        double b = 0.0;
+        if (fx[e] > 0) {
+          b = fmin(fmax((double)vv[e] * inv1r, -M), M);   // fixed in: v_j is FP64
+        } else if (fx[e] == 0) {
+          const bool w = (wide >> e) & 1u;
+          double m = 0.0;
+          bool nz;
+          if (w) {
+            m = fabs((double)vv[e]);
+            nz = m > c;
+          } else {
+            nz = mmf[e] > ccd;
+            if (nz) m = (double)mmf[e];
+          }
+          if (nz) {
+            const double r = fmax(0.0, fmin(fmin(m - c, m * inv1r), M));
+            b = ((negm >> e) & 1u) ? -r : r;
+          }
+        }
+        out[j] = (TV)b;
+      }
+    } else {
     // Standalone prox: a non-finite input, or a bounded wait of this block
     // that expired (its threshold then rests on incomplete sums), gives NaN
     // outputs instead of silently wrong ones; the counts get a sentinel below.
@@ -922,12 +1252,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
     }
     if (mode == PM_PROX && nbad > 0.0 && lbk == 0 && tid == 0) atomicCAS(a.status, ST_OK, ST_NUMERIC);
+    }
   }
 
   // ------------------------------------------------------------- epilogue
-  barrier();   // everyone is done with the round accumulators
+  barrier();   // everyone is done with the round accumulators (and, in a cluster, with every CTA's shared memory)
   if (lbk == 0) {
-    for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
+    if (!CL)
+      for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
     if (tid == 0 && mode == PM_ITER && retry) {
       // a rejected trial point: the same iteration again, with L doubled
       st->Lk *= 2.0;
