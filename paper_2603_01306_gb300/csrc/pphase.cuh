@@ -441,10 +441,19 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // S1 keys: FP64 patterns when the values are FP64 and exactness is asked for
   const bool key64 = !FAST && !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
   // FAST: the FP32 forms of the scalars
-  const double inv2l = 1.0 / (2.0 * lam2);
-  const double Mtol = M * (1.0 + 1e-6);
-  const float M32 = (float)M;
-  const float inv2l32 = (float)inv2l;
+  __shared__ double shc[2];   // 1 / (2 lambda2), M (1 + 1e-6)
+  __shared__ float shcf[2];   // M, 1 / (2 lambda2) in FP32
+  if (tid == 0) {
+    shc[0] = 1.0 / (2.0 * lam2);
+    shc[1] = M * (1.0 + 1e-6);
+    shcf[0] = (float)M;
+    shcf[1] = (float)shc[0];
+  }
+  __syncthreads();
+  const double inv2l = shc[0];
+  const double Mtol = shc[1];
+  const float M32 = shcf[0];
+  const float inv2l32 = shcf[1];
 
   int8_t fx[EPT];
   KG ka[EPT];        // S1 keys: |a| on Jf, 0 elsewhere
@@ -633,44 +642,66 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
 
   // ------------------------------------------------------ S1 / S2 setup
-  bool s1 = false, s2 = false;
-  double topsum = 0.0, gval = 0.0;
+  // The scalar decisions of each stage are taken by thread 0 and read by the
+  // others from shared memory: FP64 on this GPU is slow enough that 256
+  // copies of the same scalar arithmetic cost as much as the coordinates.
+  struct ScA {
+    double topsum, gval, w_closed;
+    unsigned long long c2lo, kc1;
+    unsigned kc2;
+    int s1, s2, w_known, g_inf, warm1, warm2;
+  };
+  __shared__ ScA sca;
+  if (tid == 0) {
+    ScA r{};
+    if (need_a) {
+      if (kb <= 0) r.topsum = 0.0;
+      else if (pb <= kb) r.topsum = tot[7];
+      else r.s1 = 1;
+    }
+    // In the loop beta^t (t >= 1) is the prox output of the last iteration,
+    // whose threshold c fixes its water level: stationarity of the prox in
+    // beta_j and the water filling in z_j give |beta_j| = |v_j| - rho w on the
+    // fractional coordinates, i.e. w = c / rho (M at most), the w of the
+    // prox's own z_j(c).  g then needs one classification at w instead of
+    // S2's rounds.
+    const double c_prev = (mode == PM_ITER) ? st->c_last : 0.0;
+    r.w_known = mode == PM_ITER && st->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
+    r.w_closed = r.w_known ? fmin(c_prev / st->rho_last, M) : 0.0;
+    if (need_b) {
+      const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
+      if (check_dom && (tot[5] > 0.0 || (kb > 0 && tot[2] > M * (double)kb * (1.0 + 1e-6)) ||
+                        (kb <= 0 && tot[2] > 0.0)))
+        r.g_inf = 1;
+      if (r.g_inf) r.gval = INFINITY;
+      else if (kb <= 0) r.gval = 0.5 * tot[1];
+      else if (tot[4] <= (double)kb) r.gval = 0.5 * (tot[1] + tot[3]);
+      else if (!r.w_known) { r.s2 = 1; r.c2lo = (unsigned long long)tot[4]; }
+    }
+    // warm first rounds from the last iteration's t* and water level (loop only)
+    const double t1p = (mode == PM_ITER) ? st->t1_last : 0.0;
+    const double w2p = (mode == PM_ITER) ? st->w2_last : 0.0;
+    r.warm1 = r.s1 && t1p > 0.0 && isfinite(t1p);
+    r.warm2 = r.s2 && w2p > 0.0 && isfinite(w2p);
+    r.kc1 = r.warm1 ? (key64 ? (unsigned long long)key_of(t1p) : (unsigned long long)key_of((float)t1p)) : 0ull;
+    r.kc2 = r.warm2 ? key_of((float)w2p) : 0u;
+    sca = r;
+  }
+  __syncthreads();
+  bool s1 = sca.s1 != 0, s2 = sca.s2 != 0;
+  double topsum = sca.topsum, gval = sca.gval;
   KG lo1 = 0, hi1 = key64 ? (KG)(KeyOf<double>::kInf + 1) : (KG)(KeyOf<float>::kInf + 1);
   KV lo2 = 0, hi2 = (KV)KeyOf<float>::kInf;
-  unsigned long long c2lo = 0, c2hi = 0;   // #{|b| > lo2}, #{|b| > hi2}
-  if (need_a) {
-    if (kb <= 0) topsum = 0.0;
-    else if (pb <= kb) topsum = tot[7];
-    else s1 = true;
-  }
-  // In the loop beta^t (t >= 1) is the prox output of the last iteration, whose
-  // threshold c fixes its water level: stationarity of the prox in beta_j and
-  // the water filling in z_j give |beta_j| = |v_j| - rho w on the fractional
-  // coordinates, i.e. w = c / rho (M at most), the w of the prox's own
-  // z_j(c).  g then needs one classification at w instead of S2's rounds.
-  const double c_prev = (mode == PM_ITER) ? st->c_last : 0.0;
-  const bool w_known = mode == PM_ITER && st->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
-  const double w_closed = w_known ? fmin(c_prev / st->rho_last, M) : 0.0;
-  bool g_inf = false;
-  if (need_b) {
-    const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
-    if (check_dom && (tot[5] > 0.0 || (kb > 0 && tot[2] > M * (double)kb * (1.0 + 1e-6)) ||
-                      (kb <= 0 && tot[2] > 0.0)))
-      g_inf = true;
-    if (g_inf) gval = INFINITY;
-    else if (kb <= 0) gval = 0.5 * tot[1];
-    else if (tot[4] <= (double)kb) gval = 0.5 * (tot[1] + tot[3]);
-    else if (!w_known) { s2 = true; c2lo = (unsigned long long)tot[4]; c2hi = 0; }
-  }
+  unsigned long long c2lo = sca.c2lo, c2hi = 0;   // #{|b| > lo2}, #{|b| > hi2}
+  const bool w_known = sca.w_known != 0;
+  const double w_closed = sca.w_closed;
+  const bool g_inf = sca.g_inf != 0;
 
   // ------------------------------------------------------- S1 / S2 rounds
-  // warm first rounds from the last iteration's t* and water level (loop only)
-  const double t1p = (mode == PM_ITER) ? st->t1_last : 0.0;
-  const double w2p = (mode == PM_ITER) ? st->w2_last : 0.0;
-  bool warm1 = s1 && t1p > 0.0 && isfinite(t1p);
-  bool warm2 = s2 && w2p > 0.0 && isfinite(w2p);
-  const KG kc1 = warm1 ? (key64 ? (KG)key_of(t1p) : (KG)key_of((float)t1p)) : (KG)0;
-  const KV kc2 = warm2 ? key_of((float)w2p) : (KV)0;
+  bool warm1 = sca.warm1 != 0;
+  bool warm2 = sca.warm2 != 0;
+  const KG kc1 = (KG)sca.kc1;
+  const KV kc2 = (KV)sca.kc2;
   const int sh1 = key64 ? 29 : 0;   // FP64 keys: 29 more mantissa bits per FP32 step
   if (retry) { s1 = false; s2 = false; warm1 = false; warm2 = false; }
   auto cand1 = [&](int q) { return warm1 ? warm_cand<KG>(kc1, lo1, hi1, q, sh1) : cand<KG>(lo1, hi1, q); };
@@ -743,15 +774,27 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // S1: t* = the kbar-th largest |a| (key lo1); TopSum = kbar H(t*) + sum (H(|a|) - H(t*))_+
   // S2: w on the bracket's piece, polished until the classification is stable.
   const bool fin1 = need_a && kb > 0 && pb > kb && !retry;
-  const double tstar = fin1 ? (key64 ? from_key((unsigned long long)lo1, 0.0)
-                                     : (double)from_key((uint32_t)lo1, 0.f)) : 0.0;
-  const double htstar = huber_d<double>(tstar, M);
-  bool pol2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb && !retry;
-  double wcur = pol2 ? (w_known ? w_closed : (double)from_key(hi2, 0.f)) : 0.0;
-  double nprev = -1.0;
-  const double wlo = (double)from_key(lo2, 0.f), whi = (double)from_key(hi2, 0.f);
+  // thread 0: the scalars of the finishing (the others read them below)
+  __shared__ double shw[5];   // htstar, wcur, topsum, gval, wlast
+  __shared__ int shw_pol2;
+  double tstar = 0.0, wlo = 0.0, whi = 0.0, nprev = -1.0;   // thread 0's
   int npol = 0;
-  double wlast = 0.0;   // the water level found (0: none)
+  if (tid == 0) {
+    tstar = fin1 ? (key64 ? from_key((unsigned long long)lo1, 0.0) : (double)from_key((uint32_t)lo1, 0.f)) : 0.0;
+    const bool p2 = need_b && !g_inf && kb > 0 && tot[4] > (double)kb && !retry;
+    shw[0] = huber_d<double>(tstar, M);
+    shw[1] = p2 ? (w_known ? w_closed : (double)from_key(hi2, 0.f)) : 0.0;
+    shw[2] = topsum;
+    shw[3] = gval;
+    shw[4] = 0.0;
+    shw_pol2 = p2;
+    wlo = (double)from_key(lo2, 0.f);
+    whi = (double)from_key(hi2, 0.f);
+  }
+  __syncthreads();
+  const double htstar = shw[0];
+  double wcur = shw[1];
+  bool pol2 = shw_pol2 != 0;
   bool first = true;
   while (first || pol2) {
     double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -803,35 +846,53 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
     gsum(v, 5);
     }
-    if (first && fin1) topsum = (double)kb * htstar + v[0];
-    first = false;
-    if (pol2) {
-      // classification at wcur: N_above, S_above, Q_above
-      const double Nab = v[2], Sab = v[3], Qab = v[4];
-      const double Sbel = tot[2] - Sab;
-      if ((double)kb - Nab <= 0.5) {   // budget filled by coordinates above: no water level
-        gval = 0.5 * (tot[1] + tot[3]);
-        pol2 = false;
-      } else {
-        const double wn = Sbel / ((double)kb - Nab);
-        // the closed-form level classifies exactly: one pass (a coordinate with
-        // |beta_j| = w adds w |beta_j| = beta_j^2 on either side)
-        const bool stable = w_known || (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
-        if (stable || npol >= MAX_POLISH) {
-          gval = 0.5 * (tot[1] + Qab + wn * Sbel);
-          wlast = wn;
-          pol2 = false;
+    if (tid == 0) {
+      if (first && fin1) shw[2] = (double)kb * htstar + v[0];
+      if (pol2) {
+        // classification at wcur: N_above, S_above, Q_above
+        const double Nab = v[2], Sab = v[3], Qab = v[4];
+        const double Sbel = tot[2] - Sab;
+        if ((double)kb - Nab <= 0.5) {   // budget filled by coordinates above: no water level
+          shw[3] = 0.5 * (tot[1] + tot[3]);
+          shw_pol2 = 0;
         } else {
-          nprev = Nab;
-          wcur = wn;
-          ++npol;
+          const double wn = Sbel / ((double)kb - Nab);
+          // the closed-form level classifies exactly: one pass (a coordinate
+          // with |beta_j| = w adds w |beta_j| = beta_j^2 on either side)
+          const bool stable = w_known || (Nab == nprev) || (wn > wlo && wn <= whi && c2lo == c2hi && npol == 0);
+          if (stable || npol >= MAX_POLISH) {
+            shw[3] = 0.5 * (tot[1] + Qab + wn * Sbel);
+            shw[4] = wn;
+            shw_pol2 = 0;
+          } else {
+            nprev = Nab;
+            shw[1] = wn;
+            ++npol;
+          }
         }
       }
     }
+    first = false;
+    __syncthreads();
+    pol2 = shw_pol2 != 0;
+    wcur = shw[1];
   }
+  topsum = shw[2];
+  gval = shw[3];
+  const double wlast = shw[4];   // the water level found (0: none)
 
   // ---------------------------------------------------------------- D
+  // thread 0 evaluates Phi, Psi and the loop's decisions; the others read
+  // what they need (stop, the best-iterate flags, the momentum)
   double phi = 0.0, psi = 0.0;
+  bool stop = false, restart = false, imp_p = false, imp_d = false;
+  double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
+  int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0, cut_rule = 0;
+  double stall_gap = 0.0;
+  const int t = st ? st->iter : 0;
+  __shared__ double shd_mu;
+  __shared__ int shd_flags;
+  if (tid == 0) {
   if (mode == PM_ITER || mode == PM_EVAL) {
     phi = Ftot + 2.0 * lam2 * gval;
     psi = Dtot - 2.0 * lam2 * (tot[0] + topsum);
@@ -848,11 +909,6 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (lbk == 0 && tid == 0) a.out[0] = tot[0] + topsum;
   }
 
-  bool stop = false, restart = false, imp_p = false, imp_d = false;
-  double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
-  int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0, cut_rule = 0;
-  double stall_gap = 0.0;
-  const int t = st ? st->iter : 0;
   if (mode == PM_ITER && !retry) {
     const double tau = st->tau;
     gap_ref = st->gap_ref;
@@ -912,6 +968,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
   }
 
+    shd_mu = mu;
+    shd_flags = (stop ? 1 : 0) | (imp_p ? 2 : 0) | (imp_d ? 4 : 0);
+  }
+  __syncthreads();
+  mu = shd_mu;
+  stop = (shd_flags & 1) != 0;
+  imp_p = (shd_flags & 2) != 0;
+  imp_d = (shd_flags & 4) != 0;
+
   // best iterates (also on the stopping iteration); for the best dual value the
   // loop's own dual point (z^t) is kept, so that the FP64 certificate
   // evaluates Psi at exactly that point
@@ -955,8 +1020,19 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (do_prox && FAST) {
     // v_j = y_j - s gy_j: FP64 where beta^t_j or beta^{t-1}_j is nonzero (or
     // j is fixed in), FP32 elsewhere, where y_j = 0
-    const float mu32 = (float)mu, s32 = (float)step, opm32 = (float)(1.0 + mu);
-    const float M1r32 = (float)(M * (1.0 + rho)), rr32 = (float)(rho / (1.0 + rho));
+    __shared__ float shv[5];   // mu, s, 1 + mu, M (1 + rho), rho / (1 + rho) in FP32
+    __shared__ int shv_mu0;
+    if (tid == 0) {
+      shv[0] = (float)mu;
+      shv[1] = (float)step;
+      shv[2] = (float)(1.0 + mu);
+      shv[3] = (float)(M * (1.0 + rho));
+      shv[4] = (float)(rho / (1.0 + rho));
+      shv_mu0 = mu == 0.0;
+    }
+    __syncthreads();
+    const float mu32 = shv[0], s32 = shv[1], opm32 = shv[2], M1r32 = shv[3], rr32 = shv[4];
+    const bool mu0 = shv_mu0 != 0;
     int c_nz = 0;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -969,8 +1045,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       if (fx[e] > 0 || !is_zero_bits(b) || !is_zero_bits(bp)) {
         double gyv;
         if (a.loss == 0) {
-          gyv = mu == 0.0 ? Gcur[j] : (1.0 + mu) * Gcur[j] - mu * Gprev[j];
-        } else if (mu == 0.0) {
+          gyv = mu0 ? Gcur[j] : (1.0 + mu) * Gcur[j] - mu * Gprev[j];
+        } else if (mu0) {
           gyv = Gcur[j];
         } else {
           gyv = 0.0;
@@ -982,8 +1058,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         wide |= 1u << e;
       } else {
         float gyv;
-        if (a.loss == 0) gyv = mu == 0.0 ? gf[e] : opm32 * gf[e] - mu32 * (float)Gprev[j];
-        else gyv = mu == 0.0 ? gf[e] : gyf[e];
+        if (a.loss == 0) gyv = mu0 ? gf[e] : opm32 * gf[e] - mu32 * (float)Gprev[j];
+        else gyv = mu0 ? gf[e] : gyf[e];
         v32 = -(s32 * gyv);
       }
       if (v32 < 0.f) negm |= 1u << e;
@@ -1056,18 +1132,41 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       nzv = nv[0];
       nbad = nv[1];
     }
-    const float inv_rho32 = (float)(1.0 / rho);
-    bool s3 = false;
+    // thread 0: the scalars of the threshold search
+    struct ScS3 {
+      double c, rhoM;
+      unsigned long long nz;
+      float inv_rho32;
+      KV kc3, krho;
+      int s3, warm3, fin;
+    };
+    __shared__ ScS3 sc3;
+    if (tid == 0) {
+      ScS3 r{};
+      if (kb <= 0) r.c = INFINITY;
+      else if (nzv <= (double)kb || nbad > 0.0) r.c = 0.0;   // no threshold search on a non-finite input
+      else r.s3 = 1;
+      r.rhoM = rho * M;
+      // for an FP32 x: rhoM > x iff x < rhoM rounded up, rhoM <= x iff x >= it
+      r.krho = key_of(__double2float_ru(r.rhoM));
+      const double c3p = (mode == PM_ITER) ? st->c_last : 0.0;
+      r.warm3 = r.s3 && c3p > 0.0 && isfinite(c3p);
+      r.kc3 = r.warm3 ? key_of((float)c3p) : (KV)0;
+      r.inv_rho32 = (float)(1.0 / rho);
+      r.nz = (unsigned long long)nzv;
+      r.fin = kb > 0 && nzv > (double)kb && nbad == 0.0;
+      sc3 = r;
+    }
+    __syncthreads();
+    c = sc3.c;
+    const float inv_rho32 = sc3.inv_rho32;
+    bool s3 = sc3.s3 != 0;
     KV lo3 = 0, hi3 = (KV)KeyOf<float>::kInf;
     // #{m > lo}, #{m > hi}, the same for T^-1
-    unsigned long long cmlo = (unsigned long long)nzv, cmhi = 0, ctlo = (unsigned long long)nzv, cthi = 0;
-    if (kb <= 0) c = INFINITY;
-    else if (nzv <= (double)kb || nbad > 0.0) c = 0.0;   // no threshold search on a non-finite input
-    else s3 = true;
-    const double rhoM = rho * M;
-    const double c3p = (mode == PM_ITER) ? st->c_last : 0.0;
-    bool warm3 = s3 && c3p > 0.0 && isfinite(c3p);
-    const KV kc3 = warm3 ? key_of((float)c3p) : (KV)0;
+    unsigned long long cmlo = sc3.nz, cmhi = 0, ctlo = sc3.nz, cthi = 0;
+    const KV krho = sc3.krho;
+    bool warm3 = sc3.warm3 != 0;
+    const KV kc3 = sc3.kc3;
     auto cand3 = [&](int q) { return warm3 ? warm_cand<KV>(kc3, lo3, hi3, q, 0) : cand<KV>(lo3, hi3, q); };
     while (s3) {
       unsigned long long fld[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -1109,22 +1208,38 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
       lo3 = nlo; hi3 = nhi; cmlo = nmlo; cmhi = nmhi; ctlo = ntlo; cthi = nthi;
       warm3 = false;
-      const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
-      const bool regime_inside = (rhoM > clo && rhoM <= chi);
+      const bool regime_inside = lo3 < krho && hi3 >= krho;   // rhoM in (c_lo, c_hi]
       if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
     }
-    if (kb > 0 && nzv > (double)kb && nbad == 0.0) {
-      // exact finishing on the bracket's piece, polished until stable
-      const double clo = (double)from_key(lo3, 0.f), chi = (double)from_key(hi3, 0.f);
-      double ccur = chi;
-      double ntop_prev = -1.0, nmid_prev = -1.0;
+    if (sc3.fin) {
+      // exact finishing on the bracket's piece, polished until stable; thread
+      // 0 takes the closed forms, every thread classifies its coordinates
+      __shared__ double shp[3];   // ccur, Tc, the root found
+      __shared__ float shpf[2];   // Tc rounded up, ccur rounded down
+      __shared__ int shp_done;
+      const double rhoM = sc3.rhoM;
+      double clo = 0.0, chi = 0.0, ntop_prev = -1.0, nmid_prev = -1.0;   // thread 0's
+      auto set_c = [&](double cc) {   // thread 0
+        const double Tc = (cc <= rhoM) ? cc * (1.0 + rho) / rho : cc + M;
+        shp[0] = cc;
+        shp[1] = Tc;
+        shpf[0] = __double2float_ru(Tc);
+        shpf[1] = __double2float_rd(cc);
+      };
+      if (tid == 0) {
+        clo = (double)from_key(lo3, 0.f);
+        chi = (double)from_key(hi3, 0.f);
+        set_c(chi);
+        shp_done = 0;
+      }
+      __syncthreads();
       for (int it = 0; it <= MAX_POLISH; ++it) {
-        const double Tc = (ccur <= rhoM) ? ccur * (1.0 + rho) / rho : ccur + M;
+        const double ccur = shp[0], Tc = shp[1];
         double v[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if constexpr (FAST) {
           // an FP32 m satisfies m >= Tc iff m >= Tc rounded up, m > ccur iff
           // m > ccur rounded down: exact classification in FP32
-          const float tcu = __double2float_ru(Tc), ccd = __double2float_rd(ccur);
+          const float tcu = shpf[0], ccd = shpf[1];
           int ntop = 0, nmid = 0;
           ffs sm{0.f, 0.f};
           for (int e = 0; e < EPT; ++e) {
@@ -1150,21 +1265,28 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         }
         gsum(v, 3);
         }
-        const double Ntop = v[0], Nmid = v[1], Smid = v[2];
-        double cn;
-        if (Nmid == 0.0) cn = ccur;   // flat piece: any c on it is a root when Ntop == kbar
-        else if (ccur <= rhoM) cn = rho * Smid / ((double)kb - Ntop + rho * Nmid);
-        else cn = (Smid - M * ((double)kb - Ntop)) / Nmid;
-        const bool inside = (it == 0) && cn > clo && cn <= chi && cmlo == cmhi && ctlo == cthi &&
-                            !(rhoM > clo && rhoM <= chi);
-        const bool stable = (Ntop == ntop_prev && Nmid == nmid_prev);
-        if (inside || stable || it == MAX_POLISH || !(cn > 0.0) || !isfinite(cn)) {
-          c = (isfinite(cn) && cn > 0.0) ? cn : ccur;
-          break;
+        if (tid == 0) {
+          const double Ntop = v[0], Nmid = v[1], Smid = v[2];
+          double cn;
+          if (Nmid == 0.0) cn = ccur;   // flat piece: any c on it is a root when Ntop == kbar
+          else if (ccur <= rhoM) cn = rho * Smid / ((double)kb - Ntop + rho * Nmid);
+          else cn = (Smid - M * ((double)kb - Ntop)) / Nmid;
+          const bool inside = (it == 0) && cn > clo && cn <= chi && cmlo == cmhi && ctlo == cthi &&
+                              !(rhoM > clo && rhoM <= chi);
+          const bool stable = (Ntop == ntop_prev && Nmid == nmid_prev);
+          if (inside || stable || it == MAX_POLISH || !(cn > 0.0) || !isfinite(cn)) {
+            shp[2] = (isfinite(cn) && cn > 0.0) ? cn : ccur;
+            shp_done = 1;
+          } else {
+            ntop_prev = Ntop;
+            nmid_prev = Nmid;
+            set_c(cn);
+          }
         }
-        ntop_prev = Ntop; nmid_prev = Nmid;
-        ccur = cn;
+        __syncthreads();
+        if (shp_done) break;
       }
+      c = shp[2];
     }
   }
 
@@ -1175,12 +1297,20 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // rotation; a retried trial point replaces the rejected one in place
     TV* out = mode == PM_ITER ? static_cast<TV*>(retry ? st->beta_cur : st->beta_prev) : static_cast<TV*>(a.vout);
     double tst[2] = {0.0, 0.0};   // backtracking: <grad F(y), x - y>, ||x - y||^2
-    const double T_c = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
+    __shared__ double shq[2];     // T_c, 1 / (1 + rho)
+    __shared__ float shq_c;       // c rounded down
+    if (tid == 0) {
+      shq[0] = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
+      shq[1] = 1.0 / (1.0 + rho);
+      shq_c = __double2float_rd(c);
+    }
+    __syncthreads();
+    const double T_c = shq[0];
     double cnt[2] = {0, 0};
     if constexpr (FAST) {
       // FP64 only for the outputs that are nonzero (about the support)
-      const double inv1r = 1.0 / (1.0 + rho);
-      const float ccd = __double2float_rd(c);   // an FP32 m exceeds c iff it exceeds ccd
+      const double inv1r = shq[1];
+      const float ccd = shq_c;   // an FP32 m exceeds c iff it exceeds ccd
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
         const int64_t j = (int64_t)gt + (int64_t)e * nthr;
