@@ -205,6 +205,23 @@ __device__ __forceinline__ ffs ff_of(double x) {
 }
 __device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
 
+// One multisection decision, taken by every warp on its own: lane q holds
+// candidate x (non-decreasing in q) and `ge`, whether its field reaches the
+// target, which holds on a prefix of the lanes (the fields do not increase
+// with the candidate).  The bracket's new lower end is the largest candidate
+// with ge, its upper end the smallest without; qlo / qhi are their lanes (-1 /
+// 32: none).
+template <typename KT>
+__device__ __forceinline__ void bracket_step(KT x, bool ge, KT& lo, KT& hi, int& qlo, int& qhi) {
+  const unsigned b = __ballot_sync(0xffffffffu, ge);
+  qlo = b ? 31 - __clz(b) : -1;
+  qhi = ~b ? __ffs(~b) - 1 : 32;
+  const KT xlo = __shfl_sync(0xffffffffu, x, qlo >= 0 ? qlo : 0);
+  const KT xhi = __shfl_sync(0xffffffffu, x, qhi < 32 ? qhi : 0);
+  if (qlo >= 0 && xlo > lo) lo = xlo; else qlo = -1;
+  if (qhi < 32 && xhi < hi) hi = xhi; else qhi = 32;
+}
+
 __device__ __forceinline__ unsigned long long fixp(float z) {
   return __float2ull_rz(z * 4294967296.0f);
 }
@@ -743,28 +760,30 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
     round_reduce(fld, 3);
     if (s1) {
-      // largest candidate with count >= kb -> new lo; smallest with count < kb -> new hi
-      KG nlo = lo1, nhi = hi1;
-      for (int q = 0; q < PQ; ++q) {
-        const KG xq = cand1(q);
-        if (sh_acc[F_S1 * PQ + q] >= (unsigned long long)kb) { if (xq > nlo) nlo = xq; }
-        else if (xq < nhi) nhi = xq;
-      }
-      lo1 = nlo; hi1 = nhi;
+      // largest candidate with count >= kb -> new lo; smallest with count < kb
+      // -> new hi.  A candidate x whose count is exactly kb ends the search:
+      // for any t with exactly kb keys at or above it, kb H(t) +
+      // sum (H(|a_j|) - H(t))_+ is the sum of the kb largest H(|a_j|)
+      // (TopSum's variational form), so t* = x serves as well as the
+      // kb-th largest key itself.
+      const unsigned long long cnt = sh_acc[F_S1 * PQ + lane];
+      int qlo, qhi;
+      bracket_step<KG>(x1, cnt >= (unsigned long long)kb, lo1, hi1, qlo, qhi);
+      const unsigned beq = __ballot_sync(0xffffffffu, cnt == (unsigned long long)kb);
       warm1 = false;
+      if (beq) {
+        lo1 = __shfl_sync(0xffffffffu, x1, 31 - __clz(beq));
+        s1 = false;
+      }
       if (hi1 - lo1 <= 1) s1 = false;
     }
     if (s2) {
-      KV nlo = lo2, nhi = hi2;
-      unsigned long long nclo = c2lo, nchi = c2hi;
       const unsigned long long thr = (unsigned long long)kb << 32;
-      for (int q = 0; q < PQ; ++q) {
-        const KV xq = cand2(q);
-        const unsigned long long cq = sh_acc[F_S2C * PQ + q];
-        if (sh_acc[F_S2Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nclo = cq; } }
-        else if (xq < nhi) { nhi = xq; nchi = cq; }
-      }
-      lo2 = nlo; hi2 = nhi; c2lo = nclo; c2hi = nchi;
+      const unsigned long long cq = sh_acc[F_S2C * PQ + lane];
+      int qlo, qhi;
+      bracket_step<KV>(x2, sh_acc[F_S2Z * PQ + lane] >= thr, lo2, hi2, qlo, qhi);
+      if (qlo >= 0) c2lo = __shfl_sync(0xffffffffu, cq, qlo);
+      if (qhi < 32) c2hi = __shfl_sync(0xffffffffu, cq, qhi);
       warm2 = false;
       if (c2lo == c2hi || hi2 - lo2 <= 1) s2 = false;
     }
@@ -805,7 +824,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       int nab = 0;
       if (first && fin1) {
         for (int e = 0; e < EPT; ++e) {
-          if (fx[e] != 0 || ka[e] < (KG)lo1) continue;
+          // keys are FP32 |a| (within two ulps of the FP64 value): a margin
+          // keeps every coordinate whose FP64 |a| exceeds t*
+          if (fx[e] != 0 || ka[e] + 4u < (KG)lo1) continue;
           const int64_t j = (int64_t)gt + (int64_t)e * nthr;
           const double hv = huber_d<double>(fabs(Gcur[j]) * inv2l, M) - htstar;
           if (hv > 0.0) ff_acc(vf[0], hv);
@@ -1197,16 +1218,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
       // fields 3..5 live at indices F_S3Z.. ; reduce fields 0..5 (0..2 unused here)
       round_reduce(fld, 6);
-      KV nlo = lo3, nhi = hi3;
-      unsigned long long nmlo = cmlo, nmhi = cmhi, ntlo = ctlo, nthi = cthi;
-      const unsigned long long thr = (unsigned long long)kb << 32;
-      for (int q = 0; q < PQ; ++q) {
-        const KV xq = cand3(q);
-        const unsigned long long cm = sh_acc[F_S3CM * PQ + q], ct = sh_acc[F_S3CT * PQ + q];
-        if (sh_acc[F_S3Z * PQ + q] >= thr) { if (xq > nlo) { nlo = xq; nmlo = cm; ntlo = ct; } }
-        else if (xq < nhi) { nhi = xq; nmhi = cm; nthi = ct; }
+      {
+        const unsigned long long thr = (unsigned long long)kb << 32;
+        const unsigned long long cm = sh_acc[F_S3CM * PQ + lane], ct = sh_acc[F_S3CT * PQ + lane];
+        int qlo, qhi;
+        bracket_step<KV>(x3, sh_acc[F_S3Z * PQ + lane] >= thr, lo3, hi3, qlo, qhi);
+        if (qlo >= 0) { cmlo = __shfl_sync(0xffffffffu, cm, qlo); ctlo = __shfl_sync(0xffffffffu, ct, qlo); }
+        if (qhi < 32) { cmhi = __shfl_sync(0xffffffffu, cm, qhi); cthi = __shfl_sync(0xffffffffu, ct, qhi); }
       }
-      lo3 = nlo; hi3 = nhi; cmlo = nmlo; cmhi = nmhi; ctlo = ntlo; cthi = nthi;
       warm3 = false;
       const bool regime_inside = lo3 < krho && hi3 >= krho;   // rhoM in (c_lo, c_hi]
       if ((cmlo == cmhi && ctlo == cthi && !regime_inside) || hi3 - lo3 <= 1) s3 = false;
