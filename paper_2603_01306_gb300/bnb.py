@@ -10,7 +10,9 @@ and measures it against the parent warm start.
 * Incumbent: the support of the k largest |beta_j| (J1 first), solved as the
   node that puts every other coordinate in J0; with no free coordinate the
   relaxation is the restricted problem itself (Eq. 1 on that support), so its
-  value is a feasible objective.
+  value is a feasible objective.  Each support is solved once (a cache keyed
+  by the support); the batched driver solves a batch's new supports in one
+  relax_solve_batch call.
 * Pruning: bound >= incumbent - rel_tol * max(1, |incumbent|).
 * Warm start of a child: the parent's beta ("parent"), or the learned start
   b + f(x) of include/warmstart.h ("learned"), which falls back to the parent's
@@ -131,11 +133,37 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
             st.fallbacks += 1
         return start
 
+    seen = {}   # support -> its restricted objective (inf: solve failed)
+
     def try_incumbent(beta_np, fix):
         f = _incumbent_fix(beta_np, fix, k)
-        _, res, code = solve(f, None, node=False)
-        if code in (0, 4) and res.primal < st.incumbent:
-            st.incumbent = res.primal
+        key = np.flatnonzero(f > 0).tobytes()
+        if key not in seen:
+            _, res, code = solve(f, None, node=False)
+            seen[key] = res.primal if code in (0, 4) else float("inf")
+        if seen[key] < st.incumbent:
+            st.incumbent = seen[key]
+
+    def try_incumbents(cands):
+        """The incumbent heuristic on several (beta, fix) at once: the new
+        supports in one batched solve."""
+        new, fixes = [], []
+        for beta_np, fix in cands:
+            f = _incumbent_fix(beta_np, fix, k)
+            key = np.flatnonzero(f > 0).tobytes()
+            if key not in seen and key not in new:
+                new.append(key)
+                fixes.append(f)
+        if fixes:
+            set_cut(False)
+            fixd = torch.tensor(np.stack(fixes), device=dev)
+            _, res, _ = h.solve_batch(len(fixes), fixings=fixd, gap_tol=gap_tol)
+            st.incumbent_solves += len(fixes)
+            for key, r in zip(new, res):
+                seen[key] = r.primal if r.status in (0, 4) else float("inf")
+        for beta_np, fix in cands:
+            key = np.flatnonzero(_incumbent_fix(beta_np, fix, k) > 0).tobytes()
+            st.incumbent = min(st.incumbent, seen[key])
 
     root = np.zeros(h.p, dtype=np.int8)
     beta, res, code = solve(root, None)
@@ -144,7 +172,7 @@ def run(h, k, max_nodes=50, gap_tol=1e-6, warm="parent", net=None, record=False,
     seq = 1
     if batch > 1:
         _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned,
-                     try_incumbent, dev, set_cut, count_cut)
+                     try_incumbents, dev, set_cut, count_cut)
         h.set_cutoff(float("inf"))
         return _finish(st, heap, t0)
     while heap and st.nodes < max_nodes:
@@ -203,7 +231,7 @@ def _children(node, k):
     return kids
 
 
-def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned, try_incumbent,
+def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, heap, st, learned, try_incumbents,
                  dev, set_cut, count_cut):
     import torch
     seq = 1 << 30
@@ -228,6 +256,7 @@ def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, he
         warmd = torch.stack([s.to(h.dtype) for s in starts]).contiguous()
         set_cut(True)
         betas, res, code = h.solve_batch(len(kids), fixings=fixd, warm_start=warmd, gap_tol=gap_tol)
+        pushed = []
         for i, (p, f) in enumerate(zip(parents, kids)):
             r = res[i]
             st.nodes += 1
@@ -244,7 +273,10 @@ def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, he
             if bound < st.incumbent - rel_tol * max(1.0, abs(st.incumbent)):
                 heapq.heappush(heap, Node(bound, seq, f, b, r.iters))
                 seq += 1
-                try_incumbent(b.double().cpu().numpy(), f)
+                pushed.append((b, f))
+        if pushed:
+            bs = torch.stack([b.double() for b, _ in pushed]).cpu().numpy()
+            try_incumbents([(bs[i], f) for i, (_, f) in enumerate(pushed)])
 
 
 def learned_start(h, net, parent_beta, fixings):

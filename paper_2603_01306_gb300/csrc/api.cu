@@ -68,6 +68,25 @@ __global__ void count_fix_kernel(const int8_t* fix, int64_t p, int* out) {
   }
 }
 
+// the same for the rows of a [rows][p] fixing matrix: row blockIdx.y into out[3 row]
+__global__ void count_fix_batch_kernel(const int8_t* fix, int64_t p, int* out) {
+  const int8_t* f = fix + (int64_t)blockIdx.y * p;
+  int j1 = 0, jf = 0, bad = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x) {
+    const int8_t v = f[j];
+    j1 += v == 1;
+    jf += v == 0;
+    bad += (v < -1 || v > 1);
+  }
+  j1 = warp_sum(j1); jf = warp_sum(jf); bad = warp_sum(bad);
+  int* o = out + 3 * blockIdx.y;
+  if ((threadIdx.x & 31) == 0) {
+    if (j1) atomicAdd(o + 0, j1);
+    if (jf) atomicAdd(o + 1, jf);
+    if (bad) atomicAdd(o + 2, bad);
+  }
+}
+
 // loop vectors are FP64; caller vectors are in the handle's dtype
 __global__ void init_vectors_kernel(const void* warm, int warm_f64, double* b0, double* b1, double* bb, double* bd,
                                     double* g0, double* g1, int64_t p, double* z0, double* z1, int64_t n) {
@@ -80,6 +99,28 @@ __global__ void init_vectors_kernel(const void* warm, int warm_f64, double* b0, 
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     z0[i] = 0.0; z1[i] = 0.0;
+  }
+}
+
+// init_vectors_kernel for node blockIdx.y of a batch: its vectors at
+// vec + nvec node (beta prev, cur; G prev, cur; beta_best, beta_dbest; then
+// from 8 p: z prev, cur), the warm start's row `node` (or zeros)
+__global__ void init_batch_kernel(const void* warm, int warm_f64, double* vec, int64_t nvec, int64_t p, int64_t n) {
+  const int node = blockIdx.y;
+  double* v = vec + nvec * node;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += stride) {
+    double w = 0.0;
+    if (warm) {
+      const int64_t q = (int64_t)node * p + j;
+      w = warm_f64 ? static_cast<const double*>(warm)[q] : (double)static_cast<const float*>(warm)[q];
+    }
+    v[j] = w; v[p + j] = w; v[4 * p + j] = w; v[5 * p + j] = w;
+    v[2 * p + j] = 0.0; v[3 * p + j] = 0.0;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    v[8 * p + i] = 0.0;
+    v[8 * p + n + i] = 0.0;
   }
 }
 
@@ -204,7 +245,45 @@ inline unsigned grid_for(int64_t work, int block = 256) {
 }  // namespace
 
 // ================================================================== handle
+// Device memory of relax_solve_batch, kept on the handle between calls
+// (grown, never shrunk) together with the CUDA graph of a round for each
+// active-set size: the graphs read only these buffers, so a later call with
+// no more nodes than `cap` replays them.  Node planes and partials are laid
+// out for `cap` nodes.
+struct BatchWs {
+  int cap = 0;
+  IterState* dst = nullptr;
+  double* vec = nullptr;
+  unsigned long long* acc = nullptr;
+  double* bpart = nullptr;
+  unsigned long long* bars = nullptr;
+  void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;   // FP64 data: operands and products
+  __nv_bfloat16 *Bp = nullptr, *Rp = nullptr;                      // FP32 data: BF16 planes of B and R
+  double *P1 = nullptr, *P2 = nullptr;                              // FP32 data: partial products per slot
+  double* part = nullptr;
+  int* active_d = nullptr;
+  int* done_d = nullptr;
+  int8_t* fix = nullptr;          // [cap][p] the call's fixings (zeros without)
+  int* cnt = nullptr;             // [cap][3] fixing counts
+  PassState* psd = nullptr;       // [cap][2] certificate passes
+  double* certd = nullptr;        // [cap][4] certificate values
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  bool planned = false, clustered = false;
+  PPlan pc;                       // cluster plan of the p-phase (when clustered)
+  void release() {
+    void* ptrs[] = {dst, vec, acc, bpart, bars, Bm, Zm, Rm, Gm, Bp, Rp, P1, P2, part, active_d, done_d, fix, cnt,
+                    psd, certd};
+    for (void* q : ptrs) if (q) cudaFree(q);
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    graphs.clear();
+    *this = BatchWs{planned, clustered, pc};
+  }
+  BatchWs() = default;
+  BatchWs(bool pl, bool cl, PPlan c) : planned(pl), clustered(cl), pc(c) {}
+};
+
 struct relax_handle {
+  BatchWs bw;                // relax_solve_batch's device memory and graphs
   // batched solves of FP32 data: BF16 planes of X (K = p) and of X' (K = n)
   // for the tensor-core products, built on the first batched call; the K
   // chunks chosen per product and column tile width (BN / 16)
@@ -285,6 +364,7 @@ void handle_free(relax_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
+  h->bw.release();
   void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xg, h->lterm, h->xcnt, h->st,
                   h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr, h->colstat};
   for (void* q : ptrs) if (q) cudaFree(q);
@@ -1459,60 +1539,103 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   const size_t es = f64 ? 8 : 4;
   const int NB = h->loss == RELAX_LS ? 1 : 2;
   std::memset(out, 0, sizeof(relax_result) * (size_t)nb);
-  // ---- per-node fixing counts
+  BatchWs& W = h->bw;
+  // ---- p-phase segments (planned once per handle): one thread-block cluster
+  // per node when p fits one cluster (hardware barriers, one launch for every
+  // node), else the fewest CTAs that cover p in cooperative waves of
+  // co-resident segments
+  if (!W.planned) {
+    W.clustered = pphase_cluster_plan(W.pc, p, h->backtrack != 0, !f64 && !h->backtrack) == cudaSuccess &&
+                  !std::getenv("RELAX_BATCH_WAVES");
+    cudaGetLastError();   // a refused cluster plan leaves no sticky error
+    W.planned = true;
+  }
+  PPlan pp = h->pp_iter;
+  const PPlan pc = W.pc;
+  const bool clustered = W.clustered;
+  const int segb = clustered ? pc.seg
+                             : (int)std::max<int64_t>(1, (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT));
+  const int wave = std::max(1, pp.maxgrid / segb);
+  if (!clustered && segb > pp.maxgrid) return RELAX_ENOTSUP;
+  // ---- device memory of the batch (the handle's, grown to nb nodes)
+  const size_t nvec = 8 * (size_t)p + 4 * (size_t)n;   // per node: 8 p-vectors, 4 n-vectors (FP64)
+  if (nb > W.cap) {
+    cudaStreamSynchronize(h->stream);
+    W.release();
+    const int cap = (nb + 63) / 64 * 64;
+    bool ok = true;
+    auto get = [&](void** q, size_t bytes) { if (ok && alloc(q, bytes) != RELAX_OK) ok = false; };
+    get((void**)&W.dst, sizeof(IterState) * (size_t)cap);
+    get((void**)&W.vec, sizeof(double) * nvec * (size_t)cap);
+    get((void**)&W.acc, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)cap);
+    get((void**)&W.bpart, sizeof(double) * 2 * (size_t)segb * NBP * (size_t)cap);
+    get((void**)&W.bars, sizeof(unsigned long long) * (size_t)cap);
+    if (f64) {
+      get(&W.Bm, es * (size_t)p * cap);
+      get(&W.Zm, es * (size_t)n * cap);
+      get(&W.Rm, es * (size_t)n * NB * cap);
+      get(&W.Gm, es * (size_t)p * NB * cap);
+    } else {
+      if (ok && ensure_planes(h) != RELAX_OK) ok = false;
+      get((void**)&W.Bp, sizeof(__nv_bfloat16) * 3 * (size_t)cap * h->ldbp);
+      get((void**)&W.Rp, sizeof(__nv_bfloat16) * 3 * (size_t)NB * cap * h->ldbn);
+      get((void**)&W.P1, sizeof(double) * BG_MAXKC * (size_t)cap * n);
+      get((void**)&W.P2, sizeof(double) * BG_MAXKC * (size_t)NB * cap * p);
+    }
+    get((void**)&W.part, sizeof(double) * (size_t)p * NB * cap);
+    get((void**)&W.active_d, sizeof(int) * (size_t)cap);
+    get((void**)&W.done_d, sizeof(int) * (size_t)cap);
+    get((void**)&W.fix, (size_t)p * cap);
+    get((void**)&W.cnt, sizeof(int) * 3 * (size_t)cap);
+    get((void**)&W.psd, sizeof(PassState) * 2 * (size_t)cap);
+    get((void**)&W.certd, sizeof(double) * 4 * (size_t)cap);
+    if (!ok) {
+      W.release();
+      return RELAX_ENOMEM;
+    }
+    if (!f64) {
+      // finite operands everywhere (rows past the active nodes are read by
+      // no product, but the planes start defined)
+      CU(cudaMemsetAsync(W.Bp, 0, sizeof(__nv_bfloat16) * 3 * (size_t)cap * h->ldbp, h->stream));
+      CU(cudaMemsetAsync(W.Rp, 0, sizeof(__nv_bfloat16) * 3 * (size_t)NB * cap * h->ldbn, h->stream));
+    }
+    W.cap = cap;
+  }
+  const int cap = W.cap;
+  IterState* dst = W.dst;
+  double* vec = W.vec;
+  unsigned long long* acc = W.acc;
+  double* bpart = W.bpart;
+  unsigned long long* bars = W.bars;
+  void *Bm = W.Bm, *Zm = W.Zm, *Rm = W.Rm, *Gm = W.Gm;
+  __nv_bfloat16 *Bp = W.Bp, *Rp = W.Rp;
+  double *P1 = W.P1, *P2 = W.P2;
+  double* part = W.part;
+  int* active_d = W.active_d;
+  int* done_d = W.done_d;
+  // ---- the call's fixings, in the workspace (the graphs read them there),
+  // and their counts per node
   std::vector<int> j1(nb, 0), jf(nb, (int)p);
   if (fixings) {
-    int* cnt = nullptr;
-    relax_status rs0 = alloc((void**)&cnt, sizeof(int) * 3 * (size_t)nb);
-    if (rs0 != RELAX_OK) return rs0;
+    CU(cudaMemcpyAsync(W.fix, fixings, (size_t)p * nb, cudaMemcpyDeviceToDevice, h->stream));
     std::vector<int> hc(3 * (size_t)nb);
-    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * 3 * (size_t)nb, h->stream);
-    for (int j = 0; j < nb && e == cudaSuccess; ++j) {
-      count_fix_kernel<<<grid_for(p), 256, 0, h->stream>>>(fixings + (size_t)j * p, p, cnt + 3 * j);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * 3 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(cnt);
-    if (e != cudaSuccess) { set_detail("fixing counts", e, __LINE__); return map_cuda(e); }
+    CU(cudaMemsetAsync(W.cnt, 0, sizeof(int) * 3 * (size_t)nb, h->stream));
+    count_fix_batch_kernel<<<dim3((unsigned)std::min<int64_t>(64, (p + 255) / 256), (unsigned)nb), 256, 0,
+                             h->stream>>>(W.fix, p, W.cnt);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(hc.data(), W.cnt, sizeof(int) * 3 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     for (int j = 0; j < nb; ++j) {
       if (hc[3 * j + 2] != 0 || hc[3 * j] > h->k) return RELAX_EINVAL;
       j1[j] = hc[3 * j];
       jf[j] = hc[3 * j + 1];
     }
+  } else {
+    CU(cudaMemsetAsync(W.fix, 0, (size_t)p * nb, h->stream));
   }
-  // ---- p-phase segments: one thread-block cluster per node when p fits one
-  // cluster (hardware barriers, one launch for every node), else the
-  // fewest CTAs that cover p in cooperative waves of co-resident segments
-  PPlan pp = h->pp_iter;
-  PPlan pc;
-  const bool clustered = pphase_cluster_plan(pc, p, h->backtrack != 0, !f64 && !h->backtrack) == cudaSuccess &&
-                         !std::getenv("RELAX_BATCH_WAVES");
-  cudaGetLastError();   // a refused cluster plan leaves no sticky error
-  const int segb = clustered ? pc.seg
-                             : (int)std::max<int64_t>(1, (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT));
-  const int wave = std::max(1, pp.maxgrid / segb);
-  if (!clustered && segb > pp.maxgrid) return RELAX_ENOTSUP;
-  // ---- device memory of the batch
-  const size_t nvec = 8 * (size_t)p + 4 * (size_t)n;   // per node: 8 p-vectors, 4 n-vectors (FP64)
-  IterState* dst = nullptr;
-  double* vec = nullptr;
-  unsigned long long* acc = nullptr;
-  double* bpart = nullptr;
-  unsigned long long* bars = nullptr;
-  void *Bm = nullptr, *Zm = nullptr, *Rm = nullptr, *Gm = nullptr;   // FP64 data: operands and products
-  __nv_bfloat16 *Bp = nullptr, *Rp = nullptr;                      // FP32 data: BF16 planes of B and R
-  double *P1 = nullptr, *P2 = nullptr;                              // FP32 data: partial products per K chunk
-  double* part = nullptr;
-  int* active_d = nullptr;
-  int* done_d = nullptr;
-  std::vector<std::pair<int, cudaGraphExec_t>> graphs;             // one round of iterations per active-set size
+  std::vector<std::pair<int, cudaGraphExec_t>>& graphs = W.graphs;   // one round of iterations per active-set size
   relax_status rs = RELAX_OK;
-  auto cleanup = [&]() {
-    void* ptrs[] = {dst, vec, acc, bpart, bars, Bm, Zm, Rm, Gm, Bp, Rp, P1, P2, part, active_d, done_d};
-    for (void* q : ptrs) if (q) cudaFree(q);
-    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
-  };
+  auto cleanup = [&]() {};
 #define BTRY(x)                    \
   do {                             \
     rs = (x);                      \
@@ -1532,30 +1655,6 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
       return map_cuda(ec_);                        \
     }                                              \
   } while (0)
-  BTRY(alloc((void**)&dst, sizeof(IterState) * (size_t)nb));
-  BTRY(alloc((void**)&vec, sizeof(double) * nvec * (size_t)nb));
-  BTRY(alloc((void**)&acc, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)nb));
-  BTRY(alloc((void**)&bpart, sizeof(double) * 2 * (size_t)segb * NBP * (size_t)nb));
-  BTRY(alloc((void**)&bars, sizeof(unsigned long long) * (size_t)nb));
-  if (f64) {
-    BTRY(alloc(&Bm, es * (size_t)p * nb));
-    BTRY(alloc(&Zm, es * (size_t)n * nb));
-    BTRY(alloc(&Rm, es * (size_t)n * NB * nb));
-    BTRY(alloc(&Gm, es * (size_t)p * NB * nb));
-  } else {
-    BTRY(ensure_planes(h));
-    const size_t bpb = sizeof(__nv_bfloat16) * 3 * (size_t)nb * h->ldbp;
-    const size_t rpb = sizeof(__nv_bfloat16) * 3 * (size_t)NB * nb * h->ldbn;
-    BTRY(alloc((void**)&Bp, bpb));
-    BTRY(alloc((void**)&Rp, rpb));
-    BTRY(alloc((void**)&P1, sizeof(double) * BG_MAXKC * (size_t)nb * n));
-    BTRY(alloc((void**)&P2, sizeof(double) * BG_MAXKC * (size_t)NB * nb * p));
-    BTRYC(cudaMemsetAsync(Bp, 0, bpb, h->stream));   // finite operands for the first timing runs
-    BTRYC(cudaMemsetAsync(Rp, 0, rpb, h->stream));
-  }
-  BTRY(alloc((void**)&part, sizeof(double) * (size_t)p * NB * nb));
-  BTRY(alloc((void**)&active_d, sizeof(int) * (size_t)nb));
-  BTRY(alloc((void**)&done_d, sizeof(int) * (size_t)nb));
   BTRYC(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3 * ACC_STRIDE * (size_t)nb, h->stream));
   BTRYC(cudaMemsetAsync(bars, 0, sizeof(unsigned long long) * (size_t)nb, h->stream));
   BTRYC(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
@@ -1594,17 +1693,15 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     s.ps.zprev = s.z_prev;
     s.ps.mom = 0.0;
     hs[j] = s;
-    const void* w = warm_start ? static_cast<const unsigned char*>(warm_start) + es * (size_t)p * j : nullptr;
-    init_vectors_kernel<<<grid_for(std::max(p, n)), 256, 0, h->stream>>>(
-        w, f64 ? 1 : 0, (double*)s.beta_prev, (double*)s.beta_cur, (double*)s.beta_best, (double*)s.beta_dbest,
-        (double*)s.G_prev, (double*)s.G_cur, p, (double*)s.z_prev, (double*)s.z_cur, n);
   }
+  init_batch_kernel<<<dim3((unsigned)std::min<int64_t>(64, (std::max(p, n) + 255) / 256), (unsigned)nb), 256, 0,
+                      h->stream>>>(warm_start, f64 ? 1 : 0, vec, (int64_t)nvec, p, n);
   BTRYC(cudaGetLastError());
   BTRYC(cudaMemcpyAsync(dst, hs.data(), sizeof(IterState) * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
   // ---- p-phase arguments (segmented)
   PArgs pa = base_pargs(h);
   pa.mode = PM_ITER;
-  pa.fix = fixings;
+  pa.fix = W.fix;
   pa.fix_stride = p;
   pa.part = part;
   pa.part_stride = (int64_t)NB * p;
@@ -1639,14 +1736,14 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
       BTRYC(bgemm_plan(pl2, (int)p, NB * m, (int)n));
       a1.tmA = h->tm_bx;
       a2.tmA = h->tm_bxt;
-      BTRYC(bgemm_encode(&a1.tmB, Bp, p, m, h->ldbp, nb, pl1.BN));
-      BTRYC(bgemm_encode(&a2.tmB, Rp, n, (int64_t)NB * m, h->ldbn, (int64_t)NB * nb, pl2.BN));
+      BTRYC(bgemm_encode(&a1.tmB, Bp, p, m, h->ldbp, cap, pl1.BN));
+      BTRYC(bgemm_encode(&a2.tmB, Rp, n, (int64_t)NB * m, h->ldbn, (int64_t)NB * cap, pl2.BN));
       fill_bgargs(a1, pl1, P1, h->status, h->limit_ns);
       fill_bgargs(a2, pl2, P2, h->status, h->limit_ns);
       io.st = dst;
       io.active = active_d;
       io.m = m;
-      io.nb = nb;
+      io.nb = cap;
       io.n = n;
       io.p = p;
       io.ldp = h->ldbp;
@@ -1752,11 +1849,8 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
   // all passes enqueued back to back, one synchronisation
   std::vector<double> cert(4 * (size_t)nb, 0.0);
   if (h->certify && map_dev_status(dstat) == RELAX_OK) {
-    PassState* psd = nullptr;
-    double* certd = nullptr;
-    BTRY(alloc((void**)&psd, sizeof(PassState) * 2 * (size_t)nb));
-    relax_status rsa = alloc((void**)&certd, sizeof(double) * 4 * (size_t)nb);
-    if (rsa != RELAX_OK) { cudaFree(psd); BTRY(rsa); }
+    PassState* psd = W.psd;
+    double* certd = W.certd;
     std::vector<PassState> pss(2 * (size_t)nb);
     for (int j = 0; j < nb; ++j) {
       PassState a{}, b{};
@@ -1775,7 +1869,7 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     relax_status rc = chk(cudaMemcpyAsync(psd, pss.data(), sizeof(PassState) * 2 * (size_t)nb,
                                           cudaMemcpyHostToDevice, h->stream), "pass states to device", __LINE__);
     for (int j = 0; j < nb && rc == RELAX_OK; ++j) {
-      const int8_t* fx = fixings ? fixings + (size_t)j * p : nullptr;
+      const int8_t* fx = fixings ? W.fix + (size_t)j * p : nullptr;
       rc = certify_enqueue(h, fx, hs[j].beta_best, true, psd + 2 * j, certd + 4 * j);
       if (rc == RELAX_OK) rc = certify_enqueue(h, fx, hs[j].beta_best, false, psd + 2 * j + 1, certd + 4 * j + 2);
     }
@@ -1784,8 +1878,6 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
                                h->stream), "certificates to host", __LINE__);
     if (rc == RELAX_OK) rc = chk(cudaStreamSynchronize(h->stream), "certificate passes", __LINE__);
     cudaStreamSynchronize(h->stream);
-    cudaFree(psd);
-    cudaFree(certd);
     BTRY(rc);
     // a non-finite certificate shows in that node's own values (judged below)
   }
