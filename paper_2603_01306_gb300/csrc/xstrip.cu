@@ -9,15 +9,16 @@
 
 namespace relax {
 
-template <typename TX, typename TA, int NF, int NB>
+template <typename TX, typename TA, int NF, int NB, bool FF = false>
 static const void* kptr() {
-  return reinterpret_cast<const void*>(&xstrip_kernel<TX, TA, NF, NB>);
+  return reinterpret_cast<const void*>(&xstrip_kernel<TX, TA, NF, NB, FF>);
 }
 
 static const void* xstrip_ptr(int xk, bool f64acc, int NF, int NB) {
   if (NF == 1 && NB == 1) {
     if (xk == XK_F64) return kptr<double, double, 1, 1>();
-    if (xk == XK_F32) return f64acc ? kptr<float, double, 1, 1>() : kptr<float, float, 1, 1>();
+    // FP32 X: the certificate / power-iteration pass in float-float arithmetic
+    if (xk == XK_F32) return f64acc ? kptr<float, float, 1, 1, true>() : kptr<float, float, 1, 1>();
     if (xk == XK_BF16 && !f64acc) return kptr<__nv_bfloat16, float, 1, 1>();
     if (xk == XK_FP8 && !f64acc) return kptr<__nv_fp8_e4m3, float, 1, 1>();
   } else if (NF == 1 && NB == 2 && !f64acc) {
@@ -27,7 +28,7 @@ static const void* xstrip_ptr(int xk, bool f64acc, int NF, int NB) {
     if (xk == XK_FP8) return kptr<__nv_fp8_e4m3, float, 1, 2>();
   } else if (NF == 2 && NB == 1) {
     if (xk == XK_F64) return kptr<double, double, 2, 1>();
-    if (xk == XK_F32 && f64acc) return kptr<float, double, 2, 1>();
+    if (xk == XK_F32 && f64acc) return kptr<float, float, 2, 1, true>();
   }
   return nullptr;
 }

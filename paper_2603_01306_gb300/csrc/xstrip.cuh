@@ -241,11 +241,18 @@ __device__ __forceinline__ void link_of(int link, const double* z, double yd, do
   }
 }
 
-template <typename TX, typename TA, int NF, int NB>
+// FF (FP32 X, TA = float): float-float arithmetic for the certificate and
+// the power iteration: each product x beta (and x r) is formed exactly as
+// the FMA pair (x bh, fma(x, bh, -x bh)) plus x bl, beta = bh + bl, and
+// summed with TwoSum (about 48 significant bits).  This GPU issues FP64 at
+// about 1/70 of the FP32 rate, which made the FP64-accumulating pass
+// compute-bound; the float-float one streams X like the loop's pass.
+template <typename TX, typename TA, int NF, int NB, bool FF = false>
 __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constant__ XSArgs a) {
   constexpr int VEC = XTraits<TX>::VEC;
   constexpr int TV = XSShape<VEC>::TV;
   constexpr bool kF32 = sizeof(TA) == 4;
+  static_assert(!FF || (sizeof(TX) == 4 && kF32), "float-float: FP32 X and FP32 pairs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t fullA[XS_MAXS], emptyA[XS_MAXS], fullB[XS_MAXS], emptyB[XS_MAXS];
   __shared__ volatile int tmo;        // a bounded wait expired: stop issuing and waiting
@@ -298,7 +305,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   }
   // phase-B accumulators (used by the axpy warps only)
   TA acc[NB][TV][VEC];
-  float ahi[kF32 ? NB : 1][TV][VEC], alo[kF32 ? NB : 1][TV][VEC];
+  float ahi[kF32 && !FF ? NB : 1][TV][VEC], alo[kF32 && !FF ? NB : 1][TV][VEC];
+  float accl[FF ? NB : 1][TV][VEC];   // FF: low parts of acc
   const bool axpy = warp >= 2 + a.SA && warp < 2 + a.SA + a.SB;
 
   if (warp == 0) {
@@ -344,6 +352,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
     // ------------------------------------------------ phase A: strip dot products
     const int st = warp - 2;
     TA bv[NF][TV][VEC];
+    float bl[FF ? NF : 1][TV][VEC];   // FF: low parts of beta
 #pragma unroll
     for (int t = 0; t < TV; ++t) {
       const int v = lane + 32 * t;
@@ -353,8 +362,11 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         const bool in = v < nvs && col < p;
         const double sc = (in && a.colscale) ? (double)a.colscale[col] : 1.0;
 #pragma unroll
-        for (int f = 0; f < NF; ++f)
-          bv[f][t][l] = in ? (TA)(static_cast<const double*>(f == 0 ? a.ps->beta : a.ps->beta2)[col] * sc) : (TA)0;
+        for (int f = 0; f < NF; ++f) {
+          const double bd = in ? static_cast<const double*>(f == 0 ? a.ps->beta : a.ps->beta2)[col] * sc : 0.0;
+          bv[f][t][l] = (TA)bd;
+          if constexpr (FF) bl[f][t][l] = (float)(bd - (double)bv[f][t][l]);
+        }
       }
     }
     if (st == 0) {
@@ -366,7 +378,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         for (int t = 0; t < TV; ++t)
 #pragma unroll
           for (int l = 0; l < VEC; ++l) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs((double)bv[f][t][l]));
+            double bb = (double)bv[f][t][l];
+            if constexpr (FF) bb += (double)bl[f][t][l];
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(bb));
             mb = bits > mb ? bits : mb;
           }
 #pragma unroll
@@ -396,10 +410,14 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       // per-lane partials of the block's rows (plain FP32 over the lane's
       // columns), then one transposed butterfly per forward vector
       TA ph[NF][XS_MAXB];
+      float phl[FF ? NF : 1][XS_MAXB];   // FF: low parts
 #pragma unroll
       for (int jj = 0; jj < XS_MAXB; ++jj) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) ph[f][jj] = (TA)0;
+        for (int f = 0; f < NF; ++f) {
+          ph[f][jj] = (TA)0;
+          if constexpr (FF) phl[f][jj] = 0.f;
+        }
         const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
         const unsigned char* rowp = tile + (size_t)jr * rowpitch;
 #pragma unroll
@@ -409,7 +427,18 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
           for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
+            for (int l = 0; l < VEC; ++l) {
+              if constexpr (FF) {
+                const float pr = x[l] * bv[f][t][l];
+                const float lo = fmaf(x[l], bl[f][t][l], fmaf(x[l], bv[f][t][l], -pr));   // exact error + x bl
+                const float sacc = ph[f][jj] + pr;
+                const float bp = sacc - ph[f][jj];
+                phl[f][jj] += ((ph[f][jj] - (sacc - bp)) + (pr - bp)) + lo;
+                ph[f][jj] = sacc;
+              } else {
+                ph[f][jj] += x[l] * bv[f][t][l];
+              }
+            }
         }
       }
       // every read of the stage is done (the partials are in registers):
@@ -420,7 +449,11 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       TA mh[NF], ml[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        if constexpr (kF32) {
+        if constexpr (FF) {
+          butterfly16(ph[f], phl[f], lane);
+          mh[f] = ph[f][0];
+          ml[f] = phl[f][0];
+        } else if constexpr (kF32) {
           float pl[XS_MAXB];
 #pragma unroll
           for (int jj = 0; jj < XS_MAXB; ++jj) pl[jj] = 0.f;
@@ -470,7 +503,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
         for (int l = 0; l < VEC; ++l) {
           acc[q][t][l] = (TA)0;
-          if constexpr (kF32) { ahi[q][t][l] = 0.f; alo[q][t][l] = 0.f; }
+          if constexpr (FF) accl[q][t][l] = 0.f;
+          else if constexpr (kF32) { ahi[q][t][l] = 0.f; alo[q][t][l] = 0.f; }
         }
     const bool need_zp = a.link == LINK_CERTZ_LS || a.link == LINK_CERTZ_LOGI || (a.link == LINK_LOGISTIC && NB > 1);
     const double* zprev = static_cast<const double*>(a.ps->zprev);
@@ -521,8 +555,13 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       for (int j = 0; j < XS_MAXB; ++j) {
         const int jr = j < a.B ? j : a.B - 1;   // rows >= rows carry weight 0
         TA w[NB];
+        float wl[FF ? NB : 1];   // FF: low parts of the row's weights
 #pragma unroll
-        for (int q = 0; q < NB; ++q) w[q] = (TA)__shfl_sync(0xffffffffu, rv[q], j);
+        for (int q = 0; q < NB; ++q) {
+          const double wd = __shfl_sync(0xffffffffu, rv[q], j);
+          w[q] = (TA)wd;
+          if constexpr (FF) wl[q] = (float)(wd - (double)w[q]);
+        }
         const unsigned char* rowp = tile + (size_t)jr * rowpitch;
 #pragma unroll
         for (int t = 0; t < TV; ++t) {
@@ -531,7 +570,18 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
           for (int l = 0; l < VEC; ++l)
 #pragma unroll
-            for (int q = 0; q < NB; ++q) acc[q][t][l] += w[q] * x[l];
+            for (int q = 0; q < NB; ++q) {
+              if constexpr (FF) {
+                const float pr = w[q] * x[l];
+                const float lo = fmaf(wl[q], x[l], fmaf(w[q], x[l], -pr));
+                const float sacc = acc[q][t][l] + pr;
+                const float bp = sacc - acc[q][t][l];
+                accl[q][t][l] += ((acc[q][t][l] - (sacc - bp)) + (pr - bp)) + lo;
+                acc[q][t][l] = sacc;
+              } else {
+                acc[q][t][l] += w[q] * x[l];
+              }
+            }
         }
       }
       __syncwarp();
@@ -539,7 +589,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         mbar_arrive(&emptyB[st]);
         atomicAdd((unsigned*)&bcnt, 1u);
       }
-      if constexpr (kF32) {   // fold the block's FP32 sums into the compensated pair
+      if constexpr (kF32 && !FF) {   // fold the block's FP32 sums into the compensated pair
 #pragma unroll
         for (int q = 0; q < NB; ++q)
 #pragma unroll
@@ -565,7 +615,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         for (int l = 0; l < VEC; ++l) {
           const int e = (lane + 32 * t) * VEC + l;
           if (e < wcols) {
-            const double v = kF32 ? (double)ahi[q][t][l] + (double)alo[q][t][l] : (double)acc[q][t][l];
+            double v;
+            if constexpr (FF) v = (double)acc[q][t][l] + (double)accl[q][t][l];
+            else v = kF32 ? (double)ahi[q][t][l] + (double)alo[q][t][l] : (double)acc[q][t][l];
             comb[((size_t)st * NB + q) * wcols + e] = v;
           }
         }
