@@ -189,7 +189,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device(device))
     relax.load()
     w, X, y = make_inputs(device, args.workload)
-    h = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M, timing=True)
+    prec = {"f32": 0, "bf16": relax.binding.RELAX_BF16, "fp8": relax.binding.RELAX_FP8E4M3}[args.precision]
+    esz = {"f32": 4, "bf16": 2, "fp8": 1}[args.precision]
+    h = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M, timing=True, precision=prec)
     stream = torch.cuda.current_stream()
     beta = torch.empty(w.p, dtype=torch.float32, device=device)
 
@@ -218,6 +220,18 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, device)
     clocks = clk.summary()
+    vs_fp32 = None
+    if prec:
+        # the same relaxation on the FP32 master X: the stored format's effect on the bound
+        h32 = relax.Handle(X, y, loss=w.loss, k=w.k, lambda2=w.lambda2, M=w.M)
+        _, r32, c32 = h32.solve(gap_tol=GAP_TOL)
+        h32.close()
+        rq = results[-1]
+        vs_fp32 = {"fp32_status": relax.STATUS[c32], "fp32_dual_bound": r32.dual_bound, "fp32_iters": r32.iters,
+                   "dual_bound": rq.dual_bound,
+                   "rel_bound_diff": (rq.dual_bound - r32.dual_bound) / max(1.0, abs(r32.dual_bound)),
+                   "note": "both bounds certified in FP64 on the FP32 master X; the stored format changes the "
+                           "loop's products only"}
     # ---- end to end through the public API, from pinned host buffers
     X_h = torch.empty(tuple(X.shape), dtype=torch.float32).pin_memory()
     y_h = torch.empty(tuple(y.shape), dtype=torch.float32).pin_memory()
@@ -250,12 +264,14 @@ def run_ours(args):
     xp_ms = sum(r.xpass_ms for r in results)
     xp_n = sum(r.xpass_count for r in results)
     pp_ms = sum(r.pphase_ms for r in results)
-    alg_bytes = w.n * w.p * 4 + 4 * (w.n + w.p)        # X once + y + beta
+    alg_bytes = w.n * w.p * esz + 4 * (w.n + w.p)      # X once (stored format) + y + beta
+    if args.precision == "fp8":
+        alg_bytes += 4 * w.p                               # per-column scales
     avg_ms = xp_ms / max(1, xp_n)
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = profile_traffic(args.workload)
+    traffic = profile_traffic(args.workload) if args.precision == "f32" else None
     value = throughput(args.steps, world, ms_max)
     line = {
         "metric": METRIC,
@@ -268,11 +284,13 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": {"f32": "f32", "bf16": "bf16 X, f32 accumulation", "fp8": "fp8-e4m3 X, f32 accumulation"}[
+            args.precision],
         "data": "synthetic (seeded AR(1) Gaussian design, generated on the device)",
-        "config": {"workload": args.workload, "n": w.n, "p": w.p, "k": w.k, "lambda2": w.lambda2,
+        "config": {"workload": args.workload, "precision": args.precision, "n": w.n, "p": w.p, "k": w.k,
+                   "lambda2": w.lambda2,
                    "rho": w.rho, "loss": w.loss, "M": w.M, "gap_tol": GAP_TOL, "snr": w.snr,
-                   "l2": f"inputs larger than L2 (X is {w.n * w.p * 4 / 1e9:.1f} GB), no flush",
+                   "l2": f"inputs larger than L2 (X is {w.n * w.p * esz / 1e9:.1f} GB as stored), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_per_relaxation": iters,
         "certified_rel_gap": max(r.rel_gap for r in results),
@@ -293,6 +311,8 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": sum(r.launches for r in results),
     }
+    if vs_fp32:
+        line["vs_fp32_solve"] = vs_fp32
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(X_h, y_h, w, results[-1].lipschitz, statistics.median(iters),
                                             args.cpu_sample_iters)
@@ -531,6 +551,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-node measurement")
+    ap.add_argument("--precision", choices=["f32", "bf16", "fp8"], default="f32",
+                    help="storage format of X in the loop (BF16, or FP8-e4m3 with per-column scales)")
     args = ap.parse_args()
     if args.impl == "reference":
         line = run_reference(args)

@@ -116,6 +116,11 @@ typedef struct {
                           fell to the cutoff (branch), 2 its Psi reached it (prune) */
   int32_t backtracks;  /* step_rule 1: rejected trial points (each doubled L); lipschitz
                           is then the final L */
+  int32_t ladder;      /* relax_solve: rungs of the precision ladder taken after the loop's
+                          own pass missed gap_tol on its arithmetic's floor (0: none; 1 the
+                          FP32 master X after a BF16 / FP8 loop; 2 float-float products on
+                          the master X).  Each rung restarts from beta_best; iters counts
+                          every rung's iterations; dual_bound is the best over the rungs. */
 } relax_result;
 
 /* Create a solver handle bound to one design X and response y (Sec. 2.3).

@@ -50,7 +50,7 @@ class Result(ctypes.Structure):
                 ("n_nz", ctypes.c_int32), ("launches", ctypes.c_int32), ("xpass_count", ctypes.c_int32),
                 ("xpass_ms", ctypes.c_double), ("pphase_ms", ctypes.c_double),
                 ("stalled", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("cutoff_rule", ctypes.c_int32), ("backtracks", ctypes.c_int32)]
+                ("cutoff_rule", ctypes.c_int32), ("backtracks", ctypes.c_int32), ("ladder", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

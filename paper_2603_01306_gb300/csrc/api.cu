@@ -320,7 +320,12 @@ struct relax_handle {
   void* y = nullptr;
   // plans
   XSPlan pl_loop, pl_cert, pl_certz, pl_ident;
-  PPlan pp_iter, pp_eval;
+  // The precision ladder of a single solve whose certified gap misses the
+  // tolerance on the loop's pass: the FP32 master X (after a BF16 / FP8
+  // loop), then float-float products on the master X; the p-phase in FP64.
+  XSPlan pl_acc32, pl_ff;
+  bool has_acc32 = false, has_ff = false;
+  PPlan pp_iter, pp_eval, pp_exact;
   // buffers
   double* xg = nullptr;          // [Gr][2][p] X' r per row group
   double* lterm = nullptr;       // [n][2] certification loss terms
@@ -842,6 +847,15 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(xstrip_plan(h->pl_ident, h->xk_loop, false, 1, 1, n, p));
     TRYC(xstrip_plan(h->pl_cert, vd ? XK_F64 : XK_F32, true, 2, 1, n, p));
     TRYC(xstrip_plan(h->pl_certz, vd ? XK_F64 : XK_F32, true, 1, 1, n, p));
+    if (!vd) {
+      const int nbl = loss == RELAX_LS ? 1 : 2;
+      TRYC(xstrip_plan(h->pl_ff, XK_F32, true, 1, nbl, n, p));
+      h->has_ff = true;
+      if (h->xk_loop == XK_BF16 || h->xk_loop == XK_FP8) {
+        TRYC(xstrip_plan(h->pl_acc32, XK_F32, false, 1, nbl, n, p));
+        h->has_acc32 = true;
+      }
+    }
     {
       const bool lowp = h->xk_loop == XK_BF16 || h->xk_loop == XK_FP8;
       const void* xl = lowp ? h->Xq : h->X;
@@ -850,6 +864,8 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       TRYC(xstrip_bind(h->pl_ident, xl, ldl, n, p));
       TRYC(xstrip_bind(h->pl_cert, h->X, h->ldx, n, p));
       TRYC(xstrip_bind(h->pl_certz, h->X, h->ldx, n, p));
+      if (h->has_ff) TRYC(xstrip_bind(h->pl_ff, h->X, h->ldx, n, p));
+      if (h->has_acc32) TRYC(xstrip_bind(h->pl_acc32, h->X, h->ldx, n, p));
       if (dtype == RELAX_F64) TRY(row_l1<double>(h->X, n, p, h->ldx, h->stream, &h->rowl1_x));
       else TRY(row_l1<float>(h->X, n, p, h->ldx, h->stream, &h->rowl1_x));
       if (h->xk_loop == XK_BF16) TRY(row_l1<__nv_bfloat16>(h->Xq, n, p, h->ldq, h->stream, &h->rowl1_q));
@@ -865,8 +881,10 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     // FP64 throughout
     TRYC(pphase_plan(h->pp_iter, true, p, h->backtrack != 0, h->xk_loop != XK_F64 && !h->backtrack));
     TRYC(pphase_plan(h->pp_eval, true, p));
+    TRYC(pphase_plan(h->pp_exact, true, p, h->backtrack != 0, false));
     {
-      const XSPlan* pls[4] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz};
+      const XSPlan* pls[6] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz,
+                              h->has_ff ? &h->pl_ff : &h->pl_loop, h->has_acc32 ? &h->pl_acc32 : &h->pl_loop};
       size_t zero_b = 0;
       int gr_max = 1;
       for (const XSPlan* q : pls) {
@@ -886,7 +904,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     for (int i = 13; i < 15; ++i) TRY(alloc(&h->vb[i], (size_t)p * sizeof(double)));
     TRY(alloc(&h->vb[15], (size_t)n * sizeof(double)));
     TRY(alloc((void**)&h->acc, 3 * ACC_STRIDE * sizeof(unsigned long long)));
-    const int gmax = std::max(h->pp_iter.grid, h->pp_eval.grid);
+    const int gmax = std::max(std::max(h->pp_iter.grid, h->pp_eval.grid), h->pp_exact.grid);
     TRY(alloc((void**)&h->bpart, (size_t)2 * gmax * NBP * sizeof(double)));
     TRY(alloc((void**)&h->bar, sizeof(unsigned long long)));
     TRY(alloc((void**)&h->bar_aux, sizeof(unsigned long long)));
@@ -1008,13 +1026,17 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     for (int i = 0; i < chunk * 3; ++i) CU(cudaEventCreate(&h->tev[i]));
   }
   cudaEvent_t* tev = h->tev;
+  // the pass and p-phase of the current rung of the precision ladder
+  const XSPlan* cur_pl = &h->pl_loop;
+  const PPlan* cur_pp = &h->pp_iter;
+  XSArgs cur_xa = xa;
   auto enqueue_body = [&](cudaStream_t cs) -> cudaError_t {
     for (int i = 0; i < chunk; ++i) {
       cudaError_t e;
       if (timing && (e = cudaEventRecordWithFlags(tev[3 * i], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      if ((e = run_pass(h, h->pl_loop, xa, cs)) != cudaSuccess) return e;
+      if ((e = run_pass(h, *cur_pl, cur_xa, cs)) != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      if ((e = pphase_launch(h->pp_iter, pa, cs)) != cudaSuccess) return e;
+      if ((e = pphase_launch(*cur_pp, pa, cs)) != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 2], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1042,7 +1064,7 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   }
   cudaGraphExec_t gexec = h->gexec;
   auto enqueue_chunk = [&]() -> cudaError_t {
-    if (gexec) return cudaGraphLaunch(gexec, h->stream);
+    if (gexec && cur_pl == &h->pl_loop) return cudaGraphLaunch(gexec, h->stream);   // the graph is of rung 0
     return enqueue_body(h->stream);
   };
   cudaEvent_t* ev = h->ev;
@@ -1096,42 +1118,86 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   // iterations again, and resuming stops once it no longer helps (and never
   // starts when X is stored in BF16/FP8: that gap is the quantisation's).
   int cert_rounds = 0;
-  double cert_primal = 0.0, cert_dual = 0.0, prev_crel = INFINITY;
+  double cert_primal = 0.0, cert_dual = 0.0, prev_crel = INFINITY, crel = INFINITY;
   bool have_cert = false;
-  const bool quantized = h->xk_loop == XK_BF16 || h->xk_loop == XK_FP8;
-  for (;;) {
-    if (err != cudaSuccess) break;
-    CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
-    int dst0 = 0;
-    CU(cudaMemcpy(&dst0, h->status, sizeof(int), cudaMemcpyDeviceToHost));
-    account(it_before, h->h_state->iter);
-    if (dst0 != ST_OK || !h->certify) break;
-    const IterState& S0 = *h->h_state;
-    rs = certify(h, fixings, S0.beta_best, nullptr, S0.z_dbest);
-    if (rs != RELAX_OK) return rs;
-    const double phi = h->h_d[0];
-    double psi = h->h_d[1];
-    rs = certify(h, fixings, S0.beta_best, S0.beta_best, nullptr);
-    if (rs != RELAX_OK) return rs;
-    if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
-    out->launches += 4;
-    have_cert = true;
-    cert_primal = phi;
-    cert_dual = psi;
-    const double crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
-    if (crel <= gap_tol || S0.iter >= h->max_iters || cert_rounds >= 3 || !(crel == crel) || quantized ||
-        S0.stalled || S0.cut_rule || crel > 0.9 * prev_crel)
-      break;
-    prev_crel = crel;
-    ++cert_rounds;
-    double tol_new = S0.tol * 0.25;
-    int zero = 0;
-    CU(cudaMemcpyAsync(&h->st->tol, &tol_new, sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(&h->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(&h->st->ps.done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  bool ladder_ok = false;   // the last certification ended for the pass's precision, not a limit
+  auto cert_phase = [&]() -> relax_status {
+    const bool quantized = cur_pl->xk == XK_BF16 || cur_pl->xk == XK_FP8;
+    cert_rounds = 0;
+    prev_crel = INFINITY;
+    ladder_ok = false;
+    for (;;) {
+      if (err != cudaSuccess) break;
+      CU(cudaMemcpy(h->h_state, h->st, sizeof(IterState), cudaMemcpyDeviceToHost));
+      int dst0 = 0;
+      CU(cudaMemcpy(&dst0, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+      account(it_before, h->h_state->iter);
+      if (dst0 != ST_OK || !h->certify) break;
+      const IterState& S0 = *h->h_state;
+      relax_status r = certify(h, fixings, S0.beta_best, nullptr, S0.z_dbest);
+      if (r != RELAX_OK) return r;
+      const double phi = h->h_d[0];
+      double psi = h->h_d[1];
+      r = certify(h, fixings, S0.beta_best, S0.beta_best, nullptr);
+      if (r != RELAX_OK) return r;
+      if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
+      out->launches += 4;
+      // every rung's dual bound is valid: the best one stays
+      cert_dual = have_cert ? std::max(cert_dual, psi) : psi;
+      cert_primal = phi;
+      have_cert = true;
+      crel = (cert_primal - cert_dual) / std::max(1.0, std::fabs(cert_primal));
+      if (crel <= gap_tol || S0.iter >= h->max_iters || !(crel == crel) || S0.cut_rule) break;
+      if (quantized || S0.stalled || cert_rounds >= 3 || crel > 0.9 * prev_crel) {
+        ladder_ok = true;
+        break;
+      }
+      prev_crel = crel;
+      ++cert_rounds;
+      double tol_new = S0.tol * 0.25;
+      int zero = 0;
+      CU(cudaMemcpyAsync(&h->st->tol, &tol_new, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      CU(cudaMemcpyAsync(&h->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      CU(cudaMemcpyAsync(&h->st->ps.done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      it_before = S0.iter;
+      run_loop(std::max<int64_t>(8, (int64_t)S0.iter / (2 * chunk) + 1));
+    }
+    return RELAX_OK;
+  };
+  rs = cert_phase();
+  if (rs != RELAX_OK) return rs;
+  // Precision ladder: when the certified gap misses gap_tol because of the
+  // pass's precision (the loop stalled on its arithmetic's floor, or the
+  // loop's problem is the BF16 / FP8 copy of X), the loop goes on from
+  // beta_best on the FP32 master X, then with float-float products on it,
+  // with the FP64 p-phase.
+  for (int rung = 0; err == cudaSuccess && ladder_ok && h->certify;) {
+    if (rung == 0 && h->has_acc32) { rung = 1; cur_pl = &h->pl_acc32; }
+    else if (rung < 2 && h->has_ff) { rung = 2; cur_pl = &h->pl_ff; }
+    else break;
+    cur_pp = &h->pp_exact;
+    cur_xa = pass_args(h, *cur_pl, h->loss == RELAX_LS ? LINK_LS : LINK_LOGISTIC, &h->st->ps);
+    pa.ncl = cur_pl->Gr;
+    const int it0 = h->h_state->iter;
+    if (it0 >= h->max_iters) break;
+    // a warm start from beta_best: the first state again, the iteration count kept
+    init_vectors_kernel<<<g, 256, 0, h->stream>>>(s.beta_best, 1, (double*)h->vb[0], (double*)h->vb[1],
+                                                  (double*)h->vb[4], (double*)h->vb[5], (double*)h->vb[2],
+                                                  (double*)h->vb[3], h->p, (double*)h->vb[6], (double*)h->vb[7],
+                                                  h->n);
+    CU(cudaGetLastError());
+    IterState s2 = s;
+    s2.iter = it0;
+    *h->h_state = s2;
+    CU(cudaMemcpyAsync(h->st, h->h_state, sizeof(IterState), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
     CU(cudaStreamSynchronize(h->stream));
-    it_before = S0.iter;
-    run_loop(std::max<int64_t>(8, (int64_t)S0.iter / (2 * chunk) + 1));
+    out->ladder = rung;
+    it_before = it0;
+    run_loop(max_chunks);
+    rs = cert_phase();
+    if (rs != RELAX_OK) return rs;
   }
   if (err != cudaSuccess) {
     set_detail("loop chunk launch", err, __LINE__);
