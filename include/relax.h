@@ -106,9 +106,10 @@ typedef struct {
   int32_t status;      /* relax_status of the solve */
   int32_t n_nz;        /* nonzeros of the returned beta */
   int32_t launches;    /* CUDA kernels this call launched (incl. no-op tail of a chunk) */
-  int32_t xpass_count; /* fused X-passes that did work (iters + 1) */
+  int32_t xpass_count; /* fused X-passes on the loop's own stored X that did work (iters + 1
+                          before any rung of the precision ladder) */
   double xpass_ms;     /* options.timing: summed device time of those X-passes */
-  double pphase_ms;    /* options.timing: summed device time of the p-phase launches */
+  double pphase_ms;    /* options.timing: summed device time of their p-phase launches */
   int32_t stalled;     /* 1: the loop stopped on the stall rule (see stall_window) */
   int32_t polish_iters; /* relax_solve_batch: iterations of the single-node finish that a
                           node stalled in the batch received (0: none) */

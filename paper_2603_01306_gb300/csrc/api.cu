@@ -1030,14 +1030,20 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   const XSPlan* cur_pl = &h->pl_loop;
   const PPlan* cur_pp = &h->pp_iter;
   XSArgs cur_xa = xa;
+  // inside a capture the timing events are recorded as external graph nodes;
+  // on direct launches they are plain records
+  bool capturing = false;
+  auto rec = [&](cudaEvent_t e, cudaStream_t cs) {
+    return capturing ? cudaEventRecordWithFlags(e, cs, cudaEventRecordExternal) : cudaEventRecord(e, cs);
+  };
   auto enqueue_body = [&](cudaStream_t cs) -> cudaError_t {
     for (int i = 0; i < chunk; ++i) {
       cudaError_t e;
-      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      if (timing && (e = rec(tev[3 * i], cs)) != cudaSuccess) return e;
       if ((e = run_pass(h, *cur_pl, cur_xa, cs)) != cudaSuccess) return e;
-      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      if (timing && (e = rec(tev[3 * i + 1], cs)) != cudaSuccess) return e;
       if ((e = pphase_launch(*cur_pp, pa, cs)) != cudaSuccess) return e;
-      if (timing && (e = cudaEventRecordWithFlags(tev[3 * i + 2], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      if (timing && (e = rec(tev[3 * i + 2], cs)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
@@ -1052,7 +1058,9 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
     bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
+      capturing = true;
       const bool lok = enqueue_body(cs) == cudaSuccess;
+      capturing = false;
       ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && lok && graph;
       if (ok) ok = cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
@@ -1167,6 +1175,9 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   };
   rs = cert_phase();
   if (rs != RELAX_OK) return rs;
+  // the timing covers the loop's own pass (rung 0)
+  const double xms_loop = xms_work, pms_loop = pms_work;
+  const int passes_loop = passes_work;
   // Precision ladder: when the certified gap misses gap_tol because of the
   // pass's precision (the loop stalled on its arithmetic's floor, or the
   // loop's problem is the BF16 / FP8 copy of X), the loop goes on from
@@ -1209,10 +1220,10 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
   CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
   const IterState& S = *h->h_state;
   out->iters = S.iter;
-  out->xpass_count = passes_work;
+  out->xpass_count = passes_loop;
   if (timing) {
-    out->xpass_ms = xms_work;
-    out->pphase_ms = pms_work;
+    out->xpass_ms = xms_loop;
+    out->pphase_ms = pms_loop;
   }
   out->restarts = S.restarts;
   out->stalled = S.stalled;

@@ -205,6 +205,20 @@ __device__ __forceinline__ ffs ff_of(double x) {
 }
 __device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
 
+// The logistic loss terms of one row in FP32 (the FAST loop), t = y z:
+// log(1 + exp(-t)), and the entropy -(u log u + v log v) of u = 1/(1 + e^t),
+// v = 1 - u, written with e = exp(-|t|) <= 1 and L = log1p(e) so that
+// neither term loses its small part when the sigmoid saturates.
+__device__ __forceinline__ void logistic_terms_f(float t, float& f, float& h) {
+  const float s = fabsf(t);
+  const float e = expf(-s);
+  const float L = log1pf(e);
+  f = fmaxf(-t, 0.f) + L;
+  const float big = 1.f / (1.f + e), small = e * big;   // the two probabilities
+  // t >= 0: u = small (pays s + L), v = big (pays L); t < 0 the other way
+  h = small * (s + L) + big * L;
+}
+
 // One multisection decision, taken by every warp on its own: lane q holds
 // candidate x (non-decreasing in q) and `ge`, whether its field reaches the
 // target, which holds on a prefix of the lanes (the fields do not increase
@@ -483,6 +497,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   //       5 domain violations, 6 non-finite, 7 sum_Jf H(a), 8 F(z), 9 -F*(-zeta)
   double s0[NBP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   double fy_sum = 0.0;   // backtracking: F at the kept momentum point
+  ffs lf8{0.f, 0.f}, lf9{0.f, 0.f};   // FAST, logistic: the loss terms in float-float
   if (a.lossp) {
     // per-row loss terms written by the certification pass
     for (int64_t i = gt; i < a.n; i += nthr) {
@@ -496,6 +511,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     const double* zy = (BT && a.backtrack && st->bt_pending) ? static_cast<const double*>(st->zy_keep) : nullptr;
     for (int64_t i = gt; i < a.n; i += nthr) {
       const double yi = a.y[i], zi = zt[i];
+      if (FAST && a.loss != 0) {
+        float f, hh;
+        logistic_terms_f((float)(yi * zi), f, hh);
+        ff_acc(lf8, f);
+        ff_acc(lf9, hh);
+        continue;
+      }
       if (a.loss == 0) {
         const double d = zi - yi, zeta = -2.0 * d;
         s0[8] += d * d;
@@ -567,8 +589,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     sf[4] = ffs{(float)c_nnz, 0.f};
     sf[5] = ffs{(float)c_dom, 0.f};
     sf[6] = ffs{(float)c_bad, 0.f};
-    sf[8] = ff_of(s0[8]);
-    sf[9] = ff_of(s0[9]);
+    sf[8] = a.loss != 0 ? lf8 : ff_of(s0[8]);
+    sf[9] = a.loss != 0 ? lf9 : ff_of(s0[9]);
   } else {
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {

@@ -199,7 +199,10 @@ __device__ __forceinline__ void butterfly16(double (&h)[16], int lane) {
 // at the momentum point for the logistic loop), lf = F term at z[0],
 // ld = -F*(-zeta) term of the dual point (certification links).  zp is the
 // row's entry of ps.zprev (z of the previous iterate, or the given dual point).
-template <int NF, int NB>
+// LOWP (the loop's FP32-accumulating passes): the logistic link in FP32
+// (FP64 exp on this GPU costs about as much as streaming the row block);
+// the float-float and FP64 passes keep it in FP64.
+template <int NF, int NB, bool LOWP = false>
 __device__ __forceinline__ void link_of(int link, const double* z, double yd, double zp, double mom, double* w,
                                         double& lf, double& ld) {
 #pragma unroll
@@ -211,10 +214,19 @@ __device__ __forceinline__ void link_of(int link, const double* z, double yd, do
       w[0] = 2.0 * (z[0] - yd);
       break;
     case LINK_LOGISTIC:
-      w[0] = -yd / (1.0 + exp(yd * z[0]));
-      if (NB > 1) {
-        const double zy = (1.0 + mom) * z[0] - mom * zp;
-        w[NB - 1] = -yd / (1.0 + exp(yd * zy));
+      if constexpr (LOWP) {
+        const float yf = (float)yd;
+        w[0] = (double)(-yf / (1.0f + expf(yf * (float)z[0])));
+        if (NB > 1) {
+          const double zy = (1.0 + mom) * z[0] - mom * zp;
+          w[NB - 1] = (double)(-yf / (1.0f + expf(yf * (float)zy)));
+        }
+      } else {
+        w[0] = -yd / (1.0 + exp(yd * z[0]));
+        if (NB > 1) {
+          const double zy = (1.0 + mom) * z[0] - mom * zp;
+          w[NB - 1] = -yd / (1.0 + exp(yd * zy));
+        }
       }
       break;
     case LINK_IDENT:
@@ -537,7 +549,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
       for (int f = 0; f < NF; ++f) z[f] = (double)(long long)__ldcg(&a.zfix[(size_t)f * n + rowj]) * zinv[f];
       double rv[NB], lf, ld;
-      link_of<NF, NB>(a.link, z, yd, zp, mom, rv, lf, ld);
+      link_of<NF, NB, kF32 && !FF>(a.link, z, yd, zp, mom, rv, lf, ld);
       if (jl >= rows) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) rv[q] = 0.0;   // rows past the end carry weight 0
