@@ -454,6 +454,7 @@ PArgs base_pargs(relax_handle* h) {
   a.bpart = h->bpart;
   a.status = h->status;
   a.limit_ns = h->limit_ns;
+  a.kc = pconst_make(a.lambda2, a.M, a.step, a.rho);
   return a;
 }
 
@@ -1388,6 +1389,7 @@ static relax_status standalone(int mode, const void* vin, void* vout, int64_t p,
   a.lambda2 = lambda2;
   a.M = M;
   a.rho = rho;
+  a.kc = pconst_make(lambda2, M, 0.0, rho);
   a.fix = fix;
   a.vin = vin;
   a.vout = vout;

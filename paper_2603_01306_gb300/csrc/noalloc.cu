@@ -110,6 +110,7 @@ extern "C" relax_status prox_persp_noalloc(const void* beta_in, void* beta_out, 
   a.lambda2 = lambda2;
   a.M = M;
   a.rho = 2.0 * lambda2 * step;
+  a.kc = pconst_make(lambda2, M, step, a.rho);
   a.fix = fixings;
   a.vin = beta_in;
   a.vout = beta_out;

@@ -34,6 +34,8 @@
 // z-sums in 32.32 fixed point), so every block takes identical decisions; FP64
 // sums go through per-block partials summed in a fixed order (deterministic).
 #pragma once
+#include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
@@ -94,7 +96,45 @@ struct IterState {
   unsigned long long bar_base;  // grid-barrier counter value at the start of a launch
 };
 
+// Scalars of a launch that follow from lambda2, M, the step and eta: taken
+// once on the host (FP64 on this GPU is slow enough that a chain of scalar
+// divisions in one thread shows in every iteration).
+struct PConst {
+  double inv2l;      // 1 / (2 lambda2)
+  double Mtol;       // M (1 + 1e-6): dom g with a relative tolerance
+  double inv1r;      // 1 / (1 + rho)
+  double kTc;        // (1 + rho) / rho: T(c) = c kTc for c <= rho M
+  double rhoM;       // rho M
+  float M, inv2l_f, s_f, M1r_f, rr_f, inv_rho_f;   // FP32 forms (M (1 + rho), rho / (1 + rho))
+  uint32_t krho;     // FP32 key of rhoM rounded up
+};
+__host__ __device__ inline PConst pconst_make(double lambda2, double M, double step, double rho) {
+  PConst k;
+  k.inv2l = 1.0 / (2.0 * lambda2);
+  k.Mtol = M * (1.0 + 1e-6);
+  k.inv1r = 1.0 / (1.0 + rho);
+  k.kTc = (1.0 + rho) / rho;
+  k.rhoM = rho * M;
+  k.M = (float)M;
+  k.inv2l_f = (float)k.inv2l;
+  k.s_f = (float)step;
+  k.M1r_f = (float)(M * (1.0 + rho));
+  k.rr_f = (float)(rho / (1.0 + rho));
+  k.inv_rho_f = (float)(1.0 / rho);
+#ifdef __CUDA_ARCH__
+  const float ru = __double2float_ru(k.rhoM);
+#else
+  float ru = (float)k.rhoM;
+  if ((double)ru < k.rhoM) ru = std::nextafter(ru, INFINITY);
+#endif
+  uint32_t bits;
+  memcpy(&bits, &ru, 4);
+  k.krho = bits;
+  return k;
+}
+
 struct PArgs {
+  PConst kc;                    // pconst_make(lambda2, M, step, rho) of this launch
   int mode;
   int loss;
   int64_t p;
@@ -308,8 +348,18 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     if (blockIdx.x == 0 && tid == 0) atomicCAS(a_in.status, ST_OK, ST_INTERNAL);
     return;
   }
+  // the node's state, read once into shared memory: the scalar stages below
+  // (taken by thread 0) would otherwise wait on one global load after another
+  __shared__ IterState sst;
+  if (st) {
+    const unsigned long long* sw = reinterpret_cast<const unsigned long long*>(st);
+    unsigned long long* dw = reinterpret_cast<unsigned long long*>(&sst);
+    for (int i = tid; i < (int)(sizeof(IterState) / 8); i += PBLOCK) dw[i] = sw[i];
+  }
+  __syncthreads();
+  const IterState* sr = st ? &sst : nullptr;   // reads; the epilogue writes st
 
-  const unsigned long long bar0 = st ? st->bar_base : a.bar_base;
+  const unsigned long long bar0 = st ? sr->bar_base : a.bar_base;
   int nbar = 0;
   bool alive = true;
   auto barrier = [&]() {
@@ -450,7 +500,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   double step = a.step;
   double rho = a.rho;
   if (BT && mode == PM_ITER && a.backtrack) {
-    step = 1.0 / st->Lk;
+    step = 1.0 / sr->Lk;
     rho = 2.0 * lam2 * step;
   }
   const TV Mv = (TV)M;
@@ -461,10 +511,10 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   const double* Gprev = nullptr;
   double* Gcur = nullptr;
   if (mode == PM_ITER) {
-    bcur = static_cast<const TV*>(st->beta_cur);
-    bprev = static_cast<const TV*>(st->beta_prev);
-    Gprev = static_cast<const double*>(st->G_prev);
-    Gcur = static_cast<double*>(st->G_cur);
+    bcur = static_cast<const TV*>(sr->beta_cur);
+    bprev = static_cast<const TV*>(sr->beta_prev);
+    Gprev = static_cast<const double*>(sr->G_prev);
+    Gcur = static_cast<double*>(sr->G_cur);
   } else if (mode == PM_EVAL || mode == PM_GVAL) {
     bcur = static_cast<const TV*>(a.vin);
   }
@@ -472,19 +522,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // S1 keys: FP64 patterns when the values are FP64 and exactness is asked for
   const bool key64 = !FAST && !a.fast_s1 && (mode == PM_EVAL || sizeof(TV) == 8);
   // FAST: the FP32 forms of the scalars
-  __shared__ double shc[2];   // 1 / (2 lambda2), M (1 + 1e-6)
-  __shared__ float shcf[2];   // M, 1 / (2 lambda2) in FP32
-  if (tid == 0) {
-    shc[0] = 1.0 / (2.0 * lam2);
-    shc[1] = M * (1.0 + 1e-6);
-    shcf[0] = (float)M;
-    shcf[1] = (float)shc[0];
-  }
-  __syncthreads();
-  const double inv2l = shc[0];
-  const double Mtol = shc[1];
-  const float M32 = shcf[0];
-  const float inv2l32 = shcf[1];
+  const double inv2l = a.kc.inv2l;
+  const double Mtol = a.kc.Mtol;
+  const float M32 = a.kc.M;
+  const float inv2l32 = a.kc.inv2l_f;
+  // the step's constants (the backtracking variant changes the step in flight)
+  PConst kr = a.kc;
+  if (BT && mode == PM_ITER && a.backtrack) kr = pconst_make(lam2, M, step, rho);
 
   int8_t fx[EPT];
   KG ka[EPT];        // S1 keys: |a| on Jf, 0 elsewhere
@@ -507,8 +551,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   } else if (mode == PM_ITER) {
     // loss terms of Eq. 6-7 at z^t = X beta^t, zeta = -grad F(z^t), in FP64;
     // with a backtracking test pending, also F at the kept momentum point
-    const double* zt = static_cast<const double*>(st->z_cur);
-    const double* zy = (BT && a.backtrack && st->bt_pending) ? static_cast<const double*>(st->zy_keep) : nullptr;
+    const double* zt = static_cast<const double*>(sr->z_cur);
+    const double* zy = (BT && a.backtrack && sr->bt_pending) ? static_cast<const double*>(sr->zy_keep) : nullptr;
     for (int64_t i = gt; i < a.n; i += nthr) {
       const double yi = a.y[i], zi = zt[i];
       if (FAST && a.loss != 0) {
@@ -544,7 +588,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // coordinates, nonzero beta^t_j, and the whole free set when the
     // cardinality budget is slack) are FP64, as are their sums (float-float).
     int c_nnz = 0, c_dom = 0, c_bad = 0;
-    const bool slack = st->pbar <= st->kbar;   // TopSum = sum over the free set of H(|a|)
+    const bool slack = sr->pbar <= sr->kbar;   // TopSum = sum over the free set of H(|a|)
 #pragma unroll
     for (int i = 0; i < NBP; ++i) sf[i] = ffs{0.f, 0.f};
 #pragma unroll
@@ -640,8 +684,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
   }
   }
-  const int kbar = st ? st->kbar : 0;   // filled below for the standalone modes
-  int kb = kbar, pb = st ? st->pbar : 0;
+  const int kbar = st ? sr->kbar : 0;   // filled below for the standalone modes
+  int kb = kbar, pb = st ? sr->pbar : 0;
   double tot[NBP];
   for (int i = 0; i < NBP; ++i) tot[i] = s0[i];
   // standalone modes need |J1| and |Jf|; reuse the sum for counts
@@ -669,14 +713,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // otherwise L_k doubles and the prox is taken again from the kept y and
   // its gradient, and this iteration evaluates nothing else.
   bool retry = false;
-  if (BT && mode == PM_ITER && a.backtrack && st->bt_pending) {
+  if (BT && mode == PM_ITER && a.backtrack && sr->bt_pending) {
     gsum(&fy_sum, 1);   // uniform: every block reads the same pending flag
     const double Fy = fy_sum;
-    const double rhs = Fy + st->dgy + 0.5 * st->Lk * st->dxy2 + 1e-12 * fmax(1.0, fabs(Fy));
+    const double rhs = Fy + sr->dgy + 0.5 * sr->Lk * sr->dxy2 + 1e-12 * fmax(1.0, fabs(Fy));
     retry = Ftot > rhs;
     if (retry) {
-      step = 0.5 / st->Lk;
+      step = 0.5 / sr->Lk;
       rho = 2.0 * lam2 * step;
+      kr = pconst_make(lam2, M, step, rho);
     }
   }
 
@@ -704,11 +749,11 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // fractional coordinates, i.e. w = c / rho (M at most), the w of the
     // prox's own z_j(c).  g then needs one classification at w instead of
     // S2's rounds.
-    const double c_prev = (mode == PM_ITER) ? st->c_last : 0.0;
-    r.w_known = mode == PM_ITER && st->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
-    r.w_closed = r.w_known ? fmin(c_prev / st->rho_last, M) : 0.0;
+    const double c_prev = (mode == PM_ITER) ? sr->c_last : 0.0;
+    r.w_known = mode == PM_ITER && sr->iter >= 1 && c_prev > 0.0 && isfinite(c_prev);
+    r.w_closed = r.w_known ? fmin(c_prev / sr->rho_last, M) : 0.0;
     if (need_b) {
-      const bool check_dom = (mode != PM_ITER) || (st->iter == 0);
+      const bool check_dom = (mode != PM_ITER) || (sr->iter == 0);
       if (check_dom && (tot[5] > 0.0 || (kb > 0 && tot[2] > M * (double)kb * (1.0 + 1e-6)) ||
                         (kb <= 0 && tot[2] > 0.0)))
         r.g_inf = 1;
@@ -718,8 +763,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       else if (!r.w_known) { r.s2 = 1; r.c2lo = (unsigned long long)tot[4]; }
     }
     // warm first rounds from the last iteration's t* and water level (loop only)
-    const double t1p = (mode == PM_ITER) ? st->t1_last : 0.0;
-    const double w2p = (mode == PM_ITER) ? st->w2_last : 0.0;
+    const double t1p = (mode == PM_ITER) ? sr->t1_last : 0.0;
+    const double w2p = (mode == PM_ITER) ? sr->w2_last : 0.0;
     r.warm1 = r.s1 && t1p > 0.0 && isfinite(t1p);
     r.warm2 = r.s2 && w2p > 0.0 && isfinite(w2p);
     r.kc1 = r.warm1 ? (key64 ? (unsigned long long)key_of(t1p) : (unsigned long long)key_of((float)t1p)) : 0ull;
@@ -932,7 +977,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   double mu = 0.0, tau_new = 1.0, gap_ref = 0.0, phi_best = 0.0, psi_best = 0.0;
   int have_ref = 0, restarts = 0, stall_iter = 0, stalled = 0, cut_rule = 0;
   double stall_gap = 0.0;
-  const int t = st ? st->iter : 0;
+  const int t = st ? sr->iter : 0;
   __shared__ double shd_mu;
   __shared__ int shd_flags;
   if (tid == 0) {
@@ -953,12 +998,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
 
   if (mode == PM_ITER && !retry) {
-    const double tau = st->tau;
-    gap_ref = st->gap_ref;
-    have_ref = st->have_ref;
-    phi_best = st->phi_best;
-    psi_best = st->psi_best;
-    restarts = st->restarts;
+    const double tau = sr->tau;
+    gap_ref = sr->gap_ref;
+    have_ref = sr->have_ref;
+    phi_best = sr->phi_best;
+    psi_best = sr->psi_best;
+    restarts = sr->restarts;
     if (nonfinite) stop = true;
     if (phi < phi_best) { phi_best = phi; imp_p = true; }
     if (psi > psi_best) { psi_best = psi; imp_d = true; }
@@ -972,7 +1017,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         ++restarts;
       }
     } else if (a.method == 0 && a.restart_rule == 1) {  // function value (O'Donoghue and Candes)
-      if (t > 1 && phi > st->phi_t) {
+      if (t > 1 && phi > sr->phi_t) {
         restart = true;
         ++restarts;
       }
@@ -985,15 +1030,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       mu = (tau - 1.0) / tn;
       tau_new = tn;
     }
-    if (isfinite(phi_best) && phi_best - psi_best <= st->tol * fmax(1.0, fabs(phi_best))) stop = true;
+    if (isfinite(phi_best) && phi_best - psi_best <= sr->tol * fmax(1.0, fabs(phi_best))) stop = true;
     if (t >= a.max_iters) stop = true;
     // Stall rule: with the gap restarts of Sec. 3.4 the best gap keeps falling
     // (geometrically while the restarts fire, at least as 1/t^2 between them);
     // one that has not fallen by 10% over the last quarter of the run, and over
     // at least stall_min iterations, sits on the floor of the loop's
     // arithmetic, and further iterations cannot lower it.
-    stall_gap = st->stall_gap;
-    stall_iter = st->stall_iter;
+    stall_gap = sr->stall_gap;
+    stall_iter = sr->stall_iter;
     const double gbest = phi_best - psi_best;
     if (!(gbest >= 0.9 * stall_gap)) {
       stall_gap = gbest;
@@ -1005,9 +1050,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // Dynamic termination (Sec. 5.3): once Phi falls to the incumbent's
     // objective the node will not be pruned, so branch now; once Psi reaches
     // it the node is pruned.  Pruning wins when both hold.
-    if (st->cutoff_on) {
-      if (isfinite(phi_best) && phi_best <= st->cutoff) { stop = true; cut_rule = 1; }
-      if (psi_best >= st->cutoff) { stop = true; cut_rule = 2; }
+    if (sr->cutoff_on) {
+      if (isfinite(phi_best) && phi_best <= sr->cutoff) { stop = true; cut_rule = 1; }
+      if (psi_best >= sr->cutoff) { stop = true; cut_rule = 2; }
     }
   }
 
@@ -1024,8 +1069,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // loop's own dual point (z^t) is kept, so that the FP64 certificate
   // evaluates Psi at exactly that point
   if (mode == PM_ITER && (imp_p || imp_d)) {
-    TV* bbest = static_cast<TV*>(st->beta_best);
-    TV* bdbest = static_cast<TV*>(st->beta_dbest);
+    TV* bbest = static_cast<TV*>(sr->beta_best);
+    TV* bdbest = static_cast<TV*>(sr->beta_dbest);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
@@ -1034,8 +1079,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       if (imp_d) bdbest[j] = bt[e];
     }
     if (imp_d) {
-      const double* zt = static_cast<const double*>(st->z_cur);
-      double* zb = static_cast<double*>(st->z_dbest);
+      const double* zt = static_cast<const double*>(sr->z_cur);
+      double* zb = static_cast<double*>(sr->z_dbest);
       for (int64_t i = gt; i < a.n; i += nthr) zb[i] = zt[i];
     }
   }
@@ -1045,9 +1090,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   const bool keep = BT && mode == PM_ITER && a.backtrack;
   if (do_prox && keep && !retry) {
     // X y^t = (1 + mu) z^t - mu z^{t-1}, for the test of the next trial point
-    const double* zc = static_cast<const double*>(st->z_cur);
-    const double* zp = static_cast<const double*>(st->z_prev);
-    double* zk = static_cast<double*>(st->zy_keep);
+    const double* zc = static_cast<const double*>(sr->z_cur);
+    const double* zp = static_cast<const double*>(sr->z_prev);
+    double* zk = static_cast<double*>(sr->zy_keep);
     for (int64_t i = gt; i < a.n; i += nthr) zk[i] = (1.0 + mu) * zc[i] - mu * zp[i];
   }
   TV vv[EPT];
@@ -1063,18 +1108,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (do_prox && FAST) {
     // v_j = y_j - s gy_j: FP64 where beta^t_j or beta^{t-1}_j is nonzero (or
     // j is fixed in), FP32 elsewhere, where y_j = 0
-    __shared__ float shv[5];   // mu, s, 1 + mu, M (1 + rho), rho / (1 + rho) in FP32
+    __shared__ float shv[2];   // mu, 1 + mu in FP32
     __shared__ int shv_mu0;
     if (tid == 0) {
       shv[0] = (float)mu;
-      shv[1] = (float)step;
-      shv[2] = (float)(1.0 + mu);
-      shv[3] = (float)(M * (1.0 + rho));
-      shv[4] = (float)(rho / (1.0 + rho));
+      shv[1] = (float)(1.0 + mu);
       shv_mu0 = mu == 0.0;
     }
     __syncthreads();
-    const float mu32 = shv[0], s32 = shv[1], opm32 = shv[2], M1r32 = shv[3], rr32 = shv[4];
+    const float mu32 = shv[0], opm32 = shv[1], s32 = kr.s_f, M1r32 = kr.M1r_f, rr32 = kr.rr_f;
     const bool mu0 = shv_mu0 != 0;
     int c_nz = 0;
 #pragma unroll
@@ -1118,8 +1160,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     const TV* vin = static_cast<const TV*>(a.vin);
     const TV muv = (TV)mu;
     const TV sv = (TV)step;
-    TV* ykeep = keep ? static_cast<TV*>(st->y_keep) : nullptr;
-    TV* gkeep = keep ? static_cast<TV*>(st->gy_keep) : nullptr;
+    TV* ykeep = keep ? static_cast<TV*>(sr->y_keep) : nullptr;
+    TV* gkeep = keep ? static_cast<TV*>(sr->gy_keep) : nullptr;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int64_t j = (int64_t)gt + (int64_t)e * nthr;
@@ -1189,13 +1231,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       if (kb <= 0) r.c = INFINITY;
       else if (nzv <= (double)kb || nbad > 0.0) r.c = 0.0;   // no threshold search on a non-finite input
       else r.s3 = 1;
-      r.rhoM = rho * M;
+      r.rhoM = kr.rhoM;
       // for an FP32 x: rhoM > x iff x < rhoM rounded up, rhoM <= x iff x >= it
-      r.krho = key_of(__double2float_ru(r.rhoM));
-      const double c3p = (mode == PM_ITER) ? st->c_last : 0.0;
+      r.krho = kr.krho;
+      const double c3p = (mode == PM_ITER) ? sr->c_last : 0.0;
       r.warm3 = r.s3 && c3p > 0.0 && isfinite(c3p);
       r.kc3 = r.warm3 ? key_of((float)c3p) : (KV)0;
-      r.inv_rho32 = (float)(1.0 / rho);
+      r.inv_rho32 = kr.inv_rho_f;
       r.nz = (unsigned long long)nzv;
       r.fin = kb > 0 && nzv > (double)kb && nbad == 0.0;
       sc3 = r;
@@ -1261,7 +1303,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       const double rhoM = sc3.rhoM;
       double clo = 0.0, chi = 0.0, ntop_prev = -1.0, nmid_prev = -1.0;   // thread 0's
       auto set_c = [&](double cc) {   // thread 0
-        const double Tc = (cc <= rhoM) ? cc * (1.0 + rho) / rho : cc + M;
+        const double Tc = (cc <= rhoM) ? cc * kr.kTc : cc + M;
         shp[0] = cc;
         shp[1] = Tc;
         shpf[0] = __double2float_ru(Tc);
@@ -1336,13 +1378,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (do_prox) {
     // the next iterate goes to the buffer that becomes beta_cur after the
     // rotation; a retried trial point replaces the rejected one in place
-    TV* out = mode == PM_ITER ? static_cast<TV*>(retry ? st->beta_cur : st->beta_prev) : static_cast<TV*>(a.vout);
+    TV* out = mode == PM_ITER ? static_cast<TV*>(retry ? sr->beta_cur : sr->beta_prev) : static_cast<TV*>(a.vout);
     double tst[2] = {0.0, 0.0};   // backtracking: <grad F(y), x - y>, ||x - y||^2
     __shared__ double shq[2];     // T_c, 1 / (1 + rho)
     __shared__ float shq_c;       // c rounded down
     if (tid == 0) {
-      shq[0] = (c <= rho * M) ? c * (1.0 + rho) / rho : c + M;
-      shq[1] = 1.0 / (1.0 + rho);
+      shq[0] = (c <= kr.rhoM) ? c * kr.kTc : c + M;
+      shq[1] = kr.inv1r;
       shq_c = __double2float_rd(c);
     }
     __syncthreads();
@@ -1402,8 +1444,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
       }
       out[j] = (TV)b;
       if (keep) {   // y^t and its gradient as P1 kept them (this thread's own writes)
-        const double d = b - (double)static_cast<const TV*>(st->y_keep)[j];
-        tst[0] += (double)static_cast<const TV*>(st->gy_keep)[j] * d;
+        const double d = b - (double)static_cast<const TV*>(sr->y_keep)[j];
+        tst[0] += (double)static_cast<const TV*>(sr->gy_keep)[j] * d;
         tst[1] += d * d;
       }
     }
@@ -1427,7 +1469,12 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   }
 
   // ------------------------------------------------------------- epilogue
-  barrier();   // everyone is done with the round accumulators (and, in a cluster, with every CTA's shared memory)
+  // Everyone must be done with the round accumulators before CTA 0 clears
+  // them: in the loop of a cooperative grid the last round is followed by a
+  // finishing sum, whose barrier already ensures that; a cluster also waits
+  // until no CTA reads another's shared memory, and the standalone modes and
+  // the backtracking variant keep the barrier.
+  if (CL || BT || mode != PM_ITER) barrier();
   if (lbk == 0) {
     if (!CL)
       for (int i = tid; i < 3 * ACC_STRIDE; i += PBLOCK) a.acc[i] = 0ull;
