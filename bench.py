@@ -403,7 +403,7 @@ def run_batch(device, workload=BATCH_WORKLOAD, reps=2, singles=16):
 BNB_WORKLOAD = "bnb_2000x5000_f32"
 
 
-def run_bnb(device, workload=BNB_WORKLOAD, gen_nodes=20000, eval_nodes=20000, batch=64, epochs=3, seed=0):
+def run_bnb(device, workload=BNB_WORKLOAD, gen_nodes=60000, eval_nodes=60000, batch=64, epochs=3, seed=0):
     """The learned warm start at its configuration (X 2000 x 5000, rho 0.8,
     k 15, lambda2 0.2, LS): a batched best-first BnB from the parent start
     records its (parent, child) node solves; the network is trained on them on

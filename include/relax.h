@@ -241,6 +241,17 @@ relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g
 relax_status relax_certify(relax_handle* h, const int8_t* fixings, const void* beta_primal,
                            const void* beta_dual, double* out_host);
 
+/* relax_certify for nb points at once (the learned warm start's fallback
+ * test in a batched BnB): out_host[2 s], out_host[2 s + 1] = {Phi(b_s),
+ * Psi(-grad F(X b_s))} for the rows b_s of points.
+ *   points: device nb x p (handle dtype), row-major; fixings: device nb x p
+ *   int8 (row s for point s) or NULL; out_host: host double[2 nb].
+ * The passes of every point are enqueued back to back and the stream is
+ * synchronized once.  RELAX_EINVAL for a row of fixings with more than k
+ * coordinates in J1 or a value outside {-1, 0, 1}. */
+relax_status relax_certify_batch(relax_handle* h, int32_t nb, const int8_t* fixings, const void* points,
+                                 double* out_host);
+
 /* Release the handle and everything it allocated (not X, y, or caller buffers). */
 relax_status relax_destroy(relax_handle* h);
 

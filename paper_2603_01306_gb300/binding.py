@@ -17,6 +17,7 @@ STATUS = {0: "RELAX_OK", 1: "RELAX_EINVAL", 2: "RELAX_ENOMEM", 3: "RELAX_ECUDA",
 
 EXPORTS = ["relax_create", "relax_solve", "relax_solve_batch", "relax_set_cutoff", "relax_xpass", "relax_batch_xpass",
            "relax_certify",
+           "relax_certify_batch",
            "relax_destroy", "relax_watchdog_probe",
            "prox_persp", "prox_persp_noalloc", "gval_persp", "gstar_persp",
            "relax_mlp_features", "relax_mlp_forward", "relax_mlp_grad", "relax_mlp_adam",
@@ -82,6 +83,8 @@ def load():
     lib.relax_watchdog_probe.argtypes = [i32, ctypes.POINTER(dbl), vp]
     lib.relax_solve_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
     lib.relax_certify.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_certify_batch.argtypes = [vp, i32, vp, vp, ctypes.POINTER(dbl)]
+    lib.relax_certify_batch.restype = i32
     lib.relax_destroy.argtypes = [vp]
     lib.prox_persp.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
     lib.prox_persp_noalloc.argtypes = [vp, vp, i64, dbl, i32, dbl, dbl, vp, i32, vp, vp]
@@ -395,6 +398,18 @@ class Handle:
         self._vec(fixings, "fixings", dtype=torch.int8)
         return relax_certify(self.h, fixings, beta_primal,
                              beta_primal if beta_dual is None else beta_dual)
+
+    def certify_batch(self, points, fixings=None):
+        """relax_certify_batch: (nb, 2) float64 numpy array {Phi(b_s), Psi(-grad F(X b_s))}
+        for the rows b_s of points (nb x p, handle dtype); fixings (nb, p) int8 or None."""
+        import numpy as np
+        import torch
+        nb = int(points.shape[0])
+        self._vec(points, "points", rows=nb)
+        self._vec(fixings, "fixings", rows=nb, dtype=torch.int8)
+        out = (ctypes.c_double * (2 * nb))()
+        _check(load().relax_certify_batch(self.h, nb, _ptr(fixings), _ptr(points), out), "relax_certify_batch")
+        return np.frombuffer(out, dtype=np.float64).reshape(nb, 2).copy()
 
     def close(self):
         if self.h is not None:

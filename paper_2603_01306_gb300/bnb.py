@@ -252,8 +252,12 @@ def _run_batched(h, k, max_nodes, gap_tol, warm, net, record, rel_tol, batch, he
         st.dropped.extend(p.bound for p in parents[room:])
         parents, kids = parents[:room], kids[:room]
         fixd = torch.tensor(np.stack(kids), device=dev)
-        starts = [learned(p.beta, f) if warm == "learned" else p.beta for p, f in zip(parents, kids)]
-        warmd = torch.stack([s.to(h.dtype) for s in starts]).contiguous()
+        if warm == "learned":
+            warmd, used = learned_starts(h, net, [p.beta for p in parents], fixd)
+            st.learned_used += int(used.sum())
+            st.fallbacks += int((~used).sum())
+        else:
+            warmd = torch.stack([p.beta.to(h.dtype) for p in parents]).contiguous()
         set_cut(True)
         betas, res, code = h.solve_batch(len(kids), fixings=fixd, warm_start=warmd, gap_tol=gap_tol)
         pushed = []
@@ -291,6 +295,24 @@ def learned_start(h, net, parent_beta, fixings):
     if not (phi_l > phi_p):
         return start, True
     return parent_beta, False
+
+
+def learned_starts(h, net, parent_betas, fixd):
+    """learned_start for the children of a batch (fixd: (nb, p) device int8):
+    the features of every child, one network evaluation, and the fallback
+    test of all 2 nb starts in one relax_certify_batch call.  Returns the
+    (nb, p) starts and a boolean numpy mask of the children that kept the
+    learned start."""
+    import torch
+    nb = len(parent_betas)
+    feats = torch.cat([h.mlp_features(pb, fixd[i]) for i, pb in enumerate(parent_betas)])
+    pred = net.predict(feats).view(nb, h.p).to(h.dtype)
+    base = feats[:, 0].contiguous().view(nb, h.p).to(h.dtype)
+    vals = h.certify_batch(torch.cat([pred, base]).contiguous(), torch.cat([fixd, fixd]).contiguous())
+    used = ~(vals[:nb, 0] > vals[nb:, 0])       # the learned Phi is not higher
+    parents = torch.stack([pb.to(h.dtype) for pb in parent_betas])
+    mask = torch.tensor(used, device=pred.device)[:, None]
+    return torch.where(mask, pred, parents).contiguous(), used
 
 
 def training_rows(h, pairs):

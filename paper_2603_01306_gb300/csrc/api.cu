@@ -2138,6 +2138,64 @@ extern "C" relax_status relax_mlp_features(relax_handle* h, const void* beta_par
 }
 
 // ================================================ batched products (diagnostic)
+extern "C" relax_status relax_certify_batch(relax_handle* h, int32_t nb, const int8_t* fixings, const void* points,
+                                            double* out_host) {
+  if (!h || nb <= 0 || !points || !out_host) return RELAX_EINVAL;
+  CU(cudaSetDevice(h->dev));
+  const int64_t p = h->p;
+  // scratch: the points in FP64, their pass states, the values, the fixing counts
+  const size_t b64 = sizeof(double) * (size_t)nb * p;
+  const size_t bps = sizeof(PassState) * (size_t)nb;
+  const size_t bout = sizeof(double) * 2 * (size_t)nb;
+  const size_t bcnt = sizeof(int) * 3 * (size_t)nb;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  unsigned char* scr = nullptr;
+  relax_status rs = alloc((void**)&scr, al(b64) + al(bps) + al(bout) + al(bcnt));
+  if (rs != RELAX_OK) return rs;
+  double* pts = reinterpret_cast<double*>(scr);
+  PassState* psd = reinterpret_cast<PassState*>(scr + al(b64));
+  double* outd = reinterpret_cast<double*>(scr + al(b64) + al(bps));
+  int* cnt = reinterpret_cast<int*>(scr + al(b64) + al(bps) + al(bout));
+  auto run = [&]() -> relax_status {
+    if (fixings) {
+      std::vector<int> hc(3 * (size_t)nb);
+      CU(cudaMemsetAsync(cnt, 0, bcnt, h->stream));
+      count_fix_batch_kernel<<<dim3((unsigned)std::min<int64_t>(64, (p + 255) / 256), (unsigned)nb), 256, 0,
+                               h->stream>>>(fixings, p, cnt);
+      CU(cudaGetLastError());
+      CU(cudaMemcpyAsync(hc.data(), cnt, bcnt, cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      for (int j = 0; j < nb; ++j)
+        if (hc[3 * j + 2] != 0 || hc[3 * j] > h->k) return RELAX_EINVAL;
+    }
+    CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    to_f64_kernel<<<grid_for((int64_t)nb * p), 256, 0, h->stream>>>(points, h->f64(), pts, (int64_t)nb * p);
+    CU(cudaGetLastError());
+    std::vector<PassState> pss((size_t)nb);
+    for (int j = 0; j < nb; ++j) {
+      PassState b{};
+      b.beta = pts + (size_t)j * p;   // Phi(b) and Psi at zeta = -grad F(X b)
+      b.beta2 = b.beta;
+      pss[j] = b;
+    }
+    CU(cudaMemcpyAsync(psd, pss.data(), bps, cudaMemcpyHostToDevice, h->stream));
+    for (int j = 0; j < nb; ++j) {
+      const relax_status r = certify_enqueue(h, fixings ? fixings + (size_t)j * p : nullptr, pts + (size_t)j * p,
+                                             false, psd + j, outd + 2 * j);
+      if (r != RELAX_OK) return r;
+    }
+    CU(cudaMemcpyAsync(out_host, outd, bout, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    int dst = 0;
+    CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    return map_dev_status(dst);
+  };
+  rs = run();
+  cudaStreamSynchronize(h->stream);
+  cudaFree(scr);
+  return rs;
+}
+
 extern "C" relax_status relax_batch_xpass(relax_handle* h, int32_t nb, const void* points, double* z_out,
                                           double* g_out, double* products_ms) {
   if (!h || nb <= 0 || !points || !z_out || !g_out) return RELAX_EINVAL;

@@ -49,3 +49,40 @@ def test_sequential_and_batched_bnb(lib):
               f"incumbent {st.incumbent:.6f}, best open bound {st.best_bound:.6f}")
     # the early stops save iterations
     assert runs[1, True][0].cut_branch + runs[1, True][0].cut_prune > 0
+
+
+def test_certify_batch_matches_single_certify(lib):
+    """relax_certify_batch: the same {Phi, Psi} as relax_certify point by
+    point (same passes, enqueued together), with and without fixings; +inf
+    Phi for a point outside dom g (a nonzero on a J0 coordinate)."""
+    w = synth.Workload("cb", 300, 700, 0.6, 8, 0.5, "ls")
+    X, y = synth.make_problem_cpu(w)
+    Xd, yd = torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda")
+    h = lib.Handle(Xd, yd, loss="ls", k=w.k, lambda2=w.lambda2, M=w.M)
+    rng = np.random.default_rng(5)
+    nb = 6
+    pts = np.zeros((nb, w.p), dtype=np.float32)
+    for s in range(nb):
+        idx = rng.choice(w.p, 6, replace=False)
+        pts[s, idx] = rng.uniform(-1.5, 1.5, 6)
+    fix = np.zeros((nb, w.p), dtype=np.int8)
+    fix[1, 3:9] = -1
+    fix[2, np.flatnonzero(pts[2])[:2]] = 1
+    fix[3, np.flatnonzero(pts[3])[0]] = -1        # a nonzero in J0: outside dom g
+    pd = torch.tensor(pts, device="cuda")
+    fd = torch.tensor(fix, device="cuda")
+    got = h.certify_batch(pd, fd)
+    for s in range(nb):
+        ref = h.certify(pd[s].contiguous(), fixings=fd[s].contiguous())
+        assert got[s, 0] == ref[0] or (np.isinf(got[s, 0]) and np.isinf(ref[0]))
+        assert got[s, 1] == ref[1]
+    assert np.isinf(got[3, 0])
+    free = h.certify_batch(pd)
+    for s in range(nb):
+        ref = h.certify(pd[s].contiguous())
+        assert free[s, 0] == ref[0] and free[s, 1] == ref[1]
+    bad = fix.copy()
+    bad[0, :w.k + 1] = 1                           # more than k in J1
+    with pytest.raises(lib.RelaxError):
+        h.certify_batch(pd, torch.tensor(bad, device="cuda"))
+    h.close()
