@@ -881,7 +881,9 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     // (FP64 at a small fraction of the FP32 rate on this GPU); FP64 data keeps
     // FP64 throughout
     TRYC(pphase_plan(h->pp_iter, true, p, h->backtrack != 0, h->xk_loop != XK_F64 && !h->backtrack));
-    TRYC(pphase_plan(h->pp_eval, true, p));
+    // the certificate's evaluation: FP32 per coordinate and FP64 wherever a
+    // term of Phi or Psi is nonzero (FP32 data); FP64 throughout for FP64 data
+    TRYC(pphase_plan(h->pp_eval, true, p, false, !vd));
     TRYC(pphase_plan(h->pp_exact, true, p, h->backtrack != 0, false));
     {
       const XSPlan* pls[6] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz,

@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   if (tid == 0) sh_done = (st != nullptr) ? st->done : 0;
   __syncthreads();
   if (sh_done) return;   // uniform: every block reads the same flag
-  if (FAST && (a_in.mode != PM_ITER || st == nullptr)) {   // the host plans FAST for the loop only
+  // the host plans FAST for the loop and the certificate's evaluation only
+  if (FAST && !((a_in.mode == PM_ITER && st != nullptr) || (a_in.mode == PM_EVAL && st == nullptr))) {
     if (blockIdx.x == 0 && tid == 0) atomicCAS(a_in.status, ST_OK, ST_INTERNAL);
     return;
   }
@@ -588,7 +589,6 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     // coordinates, nonzero beta^t_j, and the whole free set when the
     // cardinality budget is slack) are FP64, as are their sums (float-float).
     int c_nnz = 0, c_dom = 0, c_bad = 0;
-    const bool slack = sr->pbar <= sr->kbar;   // TopSum = sum over the free set of H(|a|)
 #pragma unroll
     for (int i = 0; i < NBP; ++i) sf[i] = ffs{0.f, 0.f};
 #pragma unroll
@@ -603,16 +603,13 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
         G += part[((int64_t)c * a.NB) * p + j];
         if (a.NB > 1) Gy += part[((int64_t)c * a.NB + 1) * p + j];
       }
-      Gcur[j] = G;
+      if (mode == PM_ITER) Gcur[j] = G;
       gf[e] = (float)G;
       if (a.NB > 1) gyf[e] = (float)Gy;
       const float aa = fabsf(gf[e]) * inv2l32;   // |a_j| in FP32 (keys), a = -G / (2 lambda2)
       if (!isfinite(aa)) ++c_bad;
       if (f > 0) ff_acc(sf[0], huber_d<double>(fabs(G) * inv2l, M));
-      if (f == 0) {
-        ka[e] = key_of(aa);
-        if (slack) ff_acc(sf[7], huber_d<double>(fabs(G) * inv2l, M));
-      }
+      if (f == 0) ka[e] = key_of(aa);   // a slack budget's sum over the free set: in the finishing
       const TV b = bcur[j];
       bt[e] = b;
       if (!is_zero_bits((double)b)) {          // most coordinates of beta^t are zero
@@ -633,8 +630,9 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     sf[4] = ffs{(float)c_nnz, 0.f};
     sf[5] = ffs{(float)c_dom, 0.f};
     sf[6] = ffs{(float)c_bad, 0.f};
-    sf[8] = a.loss != 0 ? lf8 : ff_of(s0[8]);
-    sf[9] = a.loss != 0 ? lf9 : ff_of(s0[9]);
+    const bool own_loss = a.loss != 0 && !a.lossp && mode == PM_ITER;   // the float-float loss loop ran
+    sf[8] = own_loss ? lf8 : ff_of(s0[8]);
+    sf[9] = own_loss ? lf9 : ff_of(s0[9]);
   } else {
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
@@ -733,14 +731,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     double topsum, gval, w_closed;
     unsigned long long c2lo, kc1;
     unsigned kc2;
-    int s1, s2, w_known, g_inf, warm1, warm2;
+    int s1, s2, w_known, g_inf, warm1, warm2, slack;
   };
   __shared__ ScA sca;
   if (tid == 0) {
     ScA r{};
     if (need_a) {
       if (kb <= 0) r.topsum = 0.0;
-      else if (pb <= kb) r.topsum = tot[7];
+      else if (pb <= kb) { r.topsum = tot[7]; r.slack = FAST; }   // FAST: summed in the finishing
       else r.s1 = 1;
     }
     // In the loop beta^t (t >= 1) is the prox output of the last iteration,
@@ -860,6 +858,14 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
   // S1: t* = the kbar-th largest |a| (key lo1); TopSum = kbar H(t*) + sum (H(|a|) - H(t*))_+
   // S2: w on the bracket's piece, polished until the classification is stable.
   const bool fin1 = need_a && kb > 0 && pb > kb && !retry;
+  const bool fins = FAST && sca.slack && !retry;   // the whole free set, in FP64 (it has at most kbar coordinates)
+  // FP64 G_j: the loop's stored G^t, or the partials again (evaluation)
+  auto G64 = [&](int64_t j) {
+    if (mode == PM_ITER) return Gcur[j];
+    double G = 0.0;
+    for (int c = 0; c < a.ncl; ++c) G += part[((int64_t)c * a.NB) * p + j];
+    return G;
+  };
   // thread 0: the scalars of the finishing (the others read them below)
   __shared__ double shw[5];   // htstar, wcur, topsum, gval, wlast
   __shared__ int shw_pol2;
@@ -895,8 +901,15 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
           // keeps every coordinate whose FP64 |a| exceeds t*
           if (fx[e] != 0 || ka[e] + 4u < (KG)lo1) continue;
           const int64_t j = (int64_t)gt + (int64_t)e * nthr;
-          const double hv = huber_d<double>(fabs(Gcur[j]) * inv2l, M) - htstar;
+          const double hv = huber_d<double>(fabs(G64(j)) * inv2l, M) - htstar;
           if (hv > 0.0) ff_acc(vf[0], hv);
+        }
+      }
+      if (first && fins) {
+        for (int e = 0; e < EPT; ++e) {
+          if (fx[e] != 0) continue;
+          const int64_t j = (int64_t)gt + (int64_t)e * nthr;
+          ff_acc(vf[0], huber_d<double>(fabs(G64(j)) * inv2l, M));
         }
       }
       if (pol2) {
@@ -936,6 +949,7 @@ __global__ void __launch_bounds__(PBLOCK) pphase_kernel(const PArgs a_in) {
     }
     if (tid == 0) {
       if (first && fin1) shw[2] = (double)kb * htstar + v[0];
+      if (first && fins) shw[2] = v[0];
       if (pol2) {
         // classification at wcur: N_above, S_above, Q_above
         const double Nab = v[2], Sab = v[3], Qab = v[4];
