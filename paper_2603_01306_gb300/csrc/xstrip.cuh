@@ -423,13 +423,41 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       // columns), then one transposed butterfly per forward vector
       TA ph[NF][XS_MAXB];
       float phl[FF ? NF : 1][XS_MAXB];   // FF: low parts
+      if constexpr (FF) {
+        // float-float: one row at a time (the fully unrolled block of
+        // float-float sums outgrew the instruction cache); the row partials
+        // go to a per-lane array for the butterfly
+#pragma unroll 1
+        for (int jj = 0; jj < XS_MAXB; ++jj) {
+          float hh[NF], ll[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) { hh[f] = 0.f; ll[f] = 0.f; }
+          const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
+          const unsigned char* rowp = tile + (size_t)jr * rowpitch;
+#pragma unroll
+          for (int t = 0; t < TV; ++t) {
+            TA x[VEC];
+            XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int l = 0; l < VEC; ++l) {
+                const float pr = x[l] * bv[f][t][l];
+                const float lo = fmaf(x[l], bl[f][t][l], fmaf(x[l], bv[f][t][l], -pr));   // exact error + x bl
+                const float sacc = hh[f] + pr;
+                const float bp = sacc - hh[f];
+                ll[f] += ((hh[f] - (sacc - bp)) + (pr - bp)) + lo;
+                hh[f] = sacc;
+              }
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) { ph[f][jj] = hh[f]; phl[f][jj] = ll[f]; }
+        }
+      } else {
 #pragma unroll
       for (int jj = 0; jj < XS_MAXB; ++jj) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          ph[f][jj] = (TA)0;
-          if constexpr (FF) phl[f][jj] = 0.f;
-        }
+        for (int f = 0; f < NF; ++f) ph[f][jj] = (TA)0;
         const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
         const unsigned char* rowp = tile + (size_t)jr * rowpitch;
 #pragma unroll
@@ -439,19 +467,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
           for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) {
-              if constexpr (FF) {
-                const float pr = x[l] * bv[f][t][l];
-                const float lo = fmaf(x[l], bl[f][t][l], fmaf(x[l], bv[f][t][l], -pr));   // exact error + x bl
-                const float sacc = ph[f][jj] + pr;
-                const float bp = sacc - ph[f][jj];
-                phl[f][jj] += ((ph[f][jj] - (sacc - bp)) + (pr - bp)) + lo;
-                ph[f][jj] = sacc;
-              } else {
-                ph[f][jj] += x[l] * bv[f][t][l];
-              }
-            }
+            for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
         }
+      }
       }
       // every read of the stage is done (the partials are in registers):
       // hand it back to the producer before the butterfly
@@ -554,6 +572,15 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
         for (int q = 0; q < NB; ++q) rv[q] = 0.0;   // rows past the end carry weight 0
       }
+      // the row's weights in the accumulation type, formed once by the lane
+      // that owns the row (FF: as a float pair)
+      TA rvh[NB];
+      float rvl[FF ? NB : 1];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        rvh[q] = (TA)rv[q];
+        if constexpr (FF) rvl[q] = (float)(rv[q] - (double)rvh[q]);
+      }
       if (cc == k % a.Gc && hb == 0 && jl < rows) {   // this CTA records the block
         if (zout) zout[r0 + jl] = z[0];
         if (a.lterm) { a.lterm[2 * (r0 + jl)] = lf; a.lterm[2 * (r0 + jl) + 1] = ld; }
@@ -563,16 +590,15 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         break;
       }
       const unsigned char* tile = ringB + st * stage;
-#pragma unroll
+#pragma unroll(FF ? 1 : XS_MAXB)
       for (int j = 0; j < XS_MAXB; ++j) {
         const int jr = j < a.B ? j : a.B - 1;   // rows >= rows carry weight 0
         TA w[NB];
         float wl[FF ? NB : 1];   // FF: low parts of the row's weights
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-          const double wd = __shfl_sync(0xffffffffu, rv[q], j);
-          w[q] = (TA)wd;
-          if constexpr (FF) wl[q] = (float)(wd - (double)w[q]);
+          w[q] = __shfl_sync(0xffffffffu, rvh[q], j);
+          if constexpr (FF) wl[q] = __shfl_sync(0xffffffffu, rvl[q], j);
         }
         const unsigned char* rowp = tile + (size_t)jr * rowpitch;
 #pragma unroll
