@@ -319,7 +319,7 @@ struct relax_handle {
   int xk_loop = XK_F32;
   void* y = nullptr;
   // plans
-  XSPlan pl_loop, pl_cert, pl_certz, pl_ident;
+  XSPlan pl_loop, pl_cert, pl_certz, pl_cert2, pl_ident;
   // The precision ladder of a single solve whose certified gap misses the
   // tolerance on the loop's pass: the FP32 master X (after a BF16 / FP8
   // loop), then float-float products on the master X; the p-phase in FP64.
@@ -329,6 +329,7 @@ struct relax_handle {
   // buffers
   double* xg = nullptr;          // [Gr][2][p] X' r per row group
   double* lterm = nullptr;       // [n][2] certification loss terms
+  double* lterm2 = nullptr;      // [n][2] the same at a second dual point
   unsigned* xcnt = nullptr;      // per-pass zeroed area: block counters, max |beta|, fixed-point z
   double rowl1_x = 0.0;          // max_i ||x_i||_1 of X (NaN if X holds a NaN)
   double rowl1_q = 0.0;          // the same for the BF16/FP8 copy (stored values)
@@ -370,7 +371,7 @@ void handle_free(relax_handle* h) {
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
   h->bw.release();
-  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xg, h->lterm, h->xcnt, h->st,
+  void* ptrs[] = {h->Xown, h->Xq, h->colscale, h->y, h->xg, h->lterm, h->lterm2, h->xcnt, h->st,
                   h->ps_aux, h->acc, h->bpart, h->bar, h->bar_aux, h->status, h->dscr, h->iscr, h->colstat};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (void* q : h->vb) if (q) cudaFree(q);
@@ -421,6 +422,7 @@ XSArgs pass_args(relax_handle* h, const XSPlan& pl, int link, PassState* ps) {
   a.ps = ps;
   a.g = h->xg;
   a.lterm = nullptr;
+  a.lterm2 = nullptr;
   a.rowl1 = lowp ? h->rowl1_q : h->rowl1_x;
   xstrip_zero_layout(pl, h->xcnt, a);
   a.status = h->status;
@@ -686,11 +688,15 @@ relax_status count_fixings(relax_handle* h, const int8_t* fix, int* j1, int* jf)
 // device memory (beta = bp, beta2 = bd or NULL, zprev = z_d or NULL).  No
 // host synchronisation; consecutive calls share the handle's scratch in
 // stream order.
-relax_status certify_enqueue(relax_handle* h, const int8_t* fix, const void* bp, bool dual_from_z,
+// The dual point of a certificate: the pass state's zprev (DUAL_Z), X beta2
+// (DUAL_B2, a second product), or X beta itself (DUAL_SELF, one product).
+enum { DUAL_Z = 0, DUAL_B2 = 1, DUAL_SELF = 2 };
+
+relax_status certify_enqueue(relax_handle* h, const int8_t* fix, const void* bp, int dual,
                              PassState* ps_dev, double* out_dev) {
-  const XSPlan& pl = dual_from_z ? h->pl_certz : h->pl_cert;
-  const int link = dual_from_z ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
-                               : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
+  const XSPlan& pl = dual == DUAL_B2 ? h->pl_cert : h->pl_certz;   // NF = 2 / NF = 1
+  const int link = dual == DUAL_Z ? (h->loss == RELAX_LS ? LINK_CERTZ_LS : LINK_CERTZ_LOGI)
+                                  : (h->loss == RELAX_LS ? LINK_CERT_LS : LINK_CERT_LOGI);
   XSArgs a = pass_args(h, pl, link, ps_dev);
   a.colscale = nullptr;
   a.lterm = h->lterm;
@@ -714,6 +720,40 @@ relax_status certify_enqueue(relax_handle* h, const int8_t* fix, const void* bp,
   return RELAX_OK;
 }
 
+// Both certificates of a point in one pass (the X beta product shared): the
+// pass state holds beta = beta_best and zprev = the loop's dual-point z.  The
+// first evaluation gives (Phi(beta), Psi at the loop's dual point) in
+// out_dev[0..1], the second (Phi(beta), Psi at zeta = -grad F(X beta)) in
+// out_dev[2..3] -- the values of the two single-certificate calls.
+relax_status certify_pair_enqueue(relax_handle* h, const int8_t* fix, const void* bp, PassState* ps_dev,
+                                  double* out_dev) {
+  const XSPlan& pl = h->pl_cert2;
+  XSArgs a = pass_args(h, pl, h->loss == RELAX_LS ? LINK_CERT2_LS : LINK_CERT2_LOGI, ps_dev);
+  a.colscale = nullptr;
+  a.lterm = h->lterm;
+  a.lterm2 = h->lterm2;
+  CU(run_pass(h, pl, a, h->stream));
+  for (int q = 0; q < 2; ++q) {
+    PArgs pa = base_pargs(h);
+    pa.mode = PM_EVAL;
+    pa.fix = fix;
+    pa.part = h->xg + (size_t)q * h->p;    // partials [Gr][2][p]: right-hand side q
+    pa.ncl = pl.Gr;
+    pa.NB = 2;
+    pa.st = nullptr;
+    pa.vin = bp;
+    pa.out = out_dev + 2 * q;
+    pa.fast_s1 = 0;
+    pa.lossp = q == 0 ? h->lterm : h->lterm2;
+    pa.n = h->n;
+    pa.bar = h->bar_aux;
+    pa.bar_base = 0;
+    CU(cudaMemsetAsync(h->bar_aux, 0, sizeof(unsigned long long), h->stream));
+    CU(pphase_launch(h->pp_eval, pa, h->stream));
+  }
+  return RELAX_OK;
+}
+
 relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const void* bd, const void* zd) {
   PassState ps{};
   ps.beta = bp;
@@ -721,9 +761,24 @@ relax_status certify(relax_handle* h, const int8_t* fix, const void* bp, const v
   ps.zprev = zd;
   *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
   CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
-  relax_status rs = certify_enqueue(h, fix, bp, zd != nullptr, h->ps_aux, h->dscr);
+  const int dual = zd ? DUAL_Z : (bd == bp ? DUAL_SELF : DUAL_B2);
+  relax_status rs = certify_enqueue(h, fix, bp, dual, h->ps_aux, h->dscr);
   if (rs != RELAX_OK) return rs;
   CU(cudaMemcpyAsync(h->h_d, h->dscr, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return RELAX_OK;
+}
+
+// certify_pair_enqueue for one point, its four values in h_d[0..3]
+relax_status certify_pair(relax_handle* h, const int8_t* fix, const void* bp, const void* zd) {
+  PassState ps{};
+  ps.beta = bp;
+  ps.zprev = zd;
+  *reinterpret_cast<PassState*>(h->h_d + 1000) = ps;
+  CU(cudaMemcpyAsync(h->ps_aux, h->h_d + 1000, sizeof(PassState), cudaMemcpyHostToDevice, h->stream));
+  relax_status rs = certify_pair_enqueue(h, fix, bp, h->ps_aux, h->dscr);
+  if (rs != RELAX_OK) return rs;
+  CU(cudaMemcpyAsync(h->h_d, h->dscr, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   return RELAX_OK;
 }
@@ -848,6 +903,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(xstrip_plan(h->pl_ident, h->xk_loop, false, 1, 1, n, p));
     TRYC(xstrip_plan(h->pl_cert, vd ? XK_F64 : XK_F32, true, 2, 1, n, p));
     TRYC(xstrip_plan(h->pl_certz, vd ? XK_F64 : XK_F32, true, 1, 1, n, p));
+    TRYC(xstrip_plan(h->pl_cert2, vd ? XK_F64 : XK_F32, true, 1, 2, n, p));
     if (!vd) {
       const int nbl = loss == RELAX_LS ? 1 : 2;
       TRYC(xstrip_plan(h->pl_ff, XK_F32, true, 1, nbl, n, p));
@@ -865,6 +921,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       TRYC(xstrip_bind(h->pl_ident, xl, ldl, n, p));
       TRYC(xstrip_bind(h->pl_cert, h->X, h->ldx, n, p));
       TRYC(xstrip_bind(h->pl_certz, h->X, h->ldx, n, p));
+      TRYC(xstrip_bind(h->pl_cert2, h->X, h->ldx, n, p));
       if (h->has_ff) TRYC(xstrip_bind(h->pl_ff, h->X, h->ldx, n, p));
       if (h->has_acc32) TRYC(xstrip_bind(h->pl_acc32, h->X, h->ldx, n, p));
       if (dtype == RELAX_F64) TRY(row_l1<double>(h->X, n, p, h->ldx, h->stream, &h->rowl1_x));
@@ -886,7 +943,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     TRYC(pphase_plan(h->pp_eval, true, p, false, !vd));
     TRYC(pphase_plan(h->pp_exact, true, p, h->backtrack != 0, false));
     {
-      const XSPlan* pls[6] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz,
+      const XSPlan* pls[7] = {&h->pl_loop, &h->pl_ident, &h->pl_cert, &h->pl_certz, &h->pl_cert2,
                               h->has_ff ? &h->pl_ff : &h->pl_loop, h->has_acc32 ? &h->pl_acc32 : &h->pl_loop};
       size_t zero_b = 0;
       int gr_max = 1;
@@ -896,6 +953,7 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
       }
       TRY(alloc((void**)&h->xg, (size_t)gr_max * 2 * p * sizeof(double)));
       TRY(alloc((void**)&h->lterm, (size_t)2 * n * sizeof(double)));
+      TRY(alloc((void**)&h->lterm2, (size_t)2 * n * sizeof(double)));
       TRY(alloc((void**)&h->xcnt, zero_b));
     }
     TRY(alloc((void**)&h->st, sizeof(IterState)));
@@ -1145,14 +1203,12 @@ relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* war
       account(it_before, h->h_state->iter);
       if (dst0 != ST_OK || !h->certify) break;
       const IterState& S0 = *h->h_state;
-      relax_status r = certify(h, fixings, S0.beta_best, nullptr, S0.z_dbest);
+      relax_status r = certify_pair(h, fixings, S0.beta_best, S0.z_dbest);
       if (r != RELAX_OK) return r;
       const double phi = h->h_d[0];
       double psi = h->h_d[1];
-      r = certify(h, fixings, S0.beta_best, S0.beta_best, nullptr);
-      if (r != RELAX_OK) return r;
-      if (h->h_d[1] > psi || !(psi == psi)) psi = h->h_d[1];
-      out->launches += 4;
+      if (h->h_d[3] > psi || !(psi == psi)) psi = h->h_d[3];
+      out->launches += 3;
       // every rung's dual bound is valid: the best one stays
       cert_dual = have_cert ? std::max(cert_dual, psi) : psi;
       cert_primal = phi;
@@ -1360,7 +1416,8 @@ relax_status relax_certify(relax_handle* h, const int8_t* fixings, const void* b
   to_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>(beta_primal, h->f64(), (double*)h->vb[8], h->p);
   to_f64_kernel<<<grid_for(h->p), 256, 0, h->stream>>>(beta_dual, h->f64(), (double*)h->vb[9], h->p);
   CU(cudaGetLastError());
-  rs = certify(h, fixings, h->vb[8], h->vb[9], nullptr);
+  // one product when both points are the same vector
+  rs = certify(h, fixings, h->vb[8], beta_dual == beta_primal ? h->vb[8] : h->vb[9], nullptr);
   if (rs != RELAX_OK) return rs;
   int dst = 0;
   CU(cudaMemcpy(&dst, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1934,13 +1991,10 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
     double* certd = W.certd;
     std::vector<PassState> pss(2 * (size_t)nb);
     for (int j = 0; j < nb; ++j) {
-      PassState a{}, b{};
-      a.beta = hs[j].beta_best;            // Phi(beta_best), Psi at the loop's dual point
-      a.zprev = hs[j].z_dbest;
-      b.beta = hs[j].beta_best;            // Psi at zeta = -grad F(X beta_best)
-      b.beta2 = hs[j].beta_best;
+      PassState a{};
+      a.beta = hs[j].beta_best;            // Phi(beta_best); Psi at the loop's dual point
+      a.zprev = hs[j].z_dbest;             // and at zeta = -grad F(X beta_best)
       pss[2 * j] = a;
-      pss[2 * j + 1] = b;
     }
     auto chk = [&](cudaError_t e, const char* what, int line) {
       if (e == cudaSuccess) return RELAX_OK;
@@ -1951,8 +2005,7 @@ extern "C" relax_status relax_solve_batch(relax_handle* h, int32_t nb, const int
                                           cudaMemcpyHostToDevice, h->stream), "pass states to device", __LINE__);
     for (int j = 0; j < nb && rc == RELAX_OK; ++j) {
       const int8_t* fx = fixings ? W.fix + (size_t)j * p : nullptr;
-      rc = certify_enqueue(h, fx, hs[j].beta_best, true, psd + 2 * j, certd + 4 * j);
-      if (rc == RELAX_OK) rc = certify_enqueue(h, fx, hs[j].beta_best, false, psd + 2 * j + 1, certd + 4 * j + 2);
+      rc = certify_pair_enqueue(h, fx, hs[j].beta_best, psd + 2 * j, certd + 4 * j);
     }
     if (rc == RELAX_OK)
       rc = chk(cudaMemcpyAsync(cert.data(), certd, sizeof(double) * 4 * (size_t)nb, cudaMemcpyDeviceToHost,
@@ -2177,13 +2230,12 @@ extern "C" relax_status relax_certify_batch(relax_handle* h, int32_t nb, const i
     for (int j = 0; j < nb; ++j) {
       PassState b{};
       b.beta = pts + (size_t)j * p;   // Phi(b) and Psi at zeta = -grad F(X b)
-      b.beta2 = b.beta;
       pss[j] = b;
     }
     CU(cudaMemcpyAsync(psd, pss.data(), bps, cudaMemcpyHostToDevice, h->stream));
     for (int j = 0; j < nb; ++j) {
       const relax_status r = certify_enqueue(h, fixings ? fixings + (size_t)j * p : nullptr, pts + (size_t)j * p,
-                                             false, psd + j, outd + 2 * j);
+                                             DUAL_SELF, psd + j, outd + 2 * j);
       if (r != RELAX_OK) return r;
     }
     CU(cudaMemcpyAsync(out_host, outd, bout, cudaMemcpyDeviceToHost, h->stream));

@@ -17,6 +17,12 @@ enum Link : int {
   LINK_CERT_LOGI = 4,  // NF=2 NB=1: F at z0, r = grad at z1
   LINK_CERTZ_LS = 5,   // NF=1 NB=1: F at z0, r = 2(zd - y) with zd = ps.zprev (given dual point)
   LINK_CERTZ_LOGI = 6, // NF=1 NB=1: F at z0, r = grad at zd
+  // both dual points of a certificate in one pass: NF=1 NB=2, F at z0,
+  // r0 = the link at zd = ps.zprev (the loop's best dual point), r1 = the link
+  // at z0 (zeta = -grad F(X beta)); lterm gets {F, dual term at zd}, lterm2
+  // {F, dual term at z0}
+  LINK_CERT2_LS = 7,
+  LINK_CERT2_LOGI = 8,
 };
 
 // Device-resident solver state that the pass reads (pointers rotate between

@@ -22,7 +22,9 @@ static const void* xstrip_ptr(int xk, bool f64acc, int NF, int NB) {
     if (xk == XK_BF16 && !f64acc) return kptr<__nv_bfloat16, float, 1, 1>();
     if (xk == XK_FP8 && !f64acc) return kptr<__nv_fp8_e4m3, float, 1, 1>();
   } else if (NF == 1 && NB == 2 && f64acc) {
-    if (xk == XK_F32) return kptr<float, float, 1, 2, true>();   // the logistic loop's float-float pass
+    // the logistic loop's float-float pass; the two-dual-point certificate
+    if (xk == XK_F32) return kptr<float, float, 1, 2, true>();
+    if (xk == XK_F64) return kptr<double, double, 1, 2>();
   } else if (NF == 1 && NB == 2 && !f64acc) {
     if (xk == XK_F64) return kptr<double, double, 1, 2>();
     if (xk == XK_F32) return kptr<float, float, 1, 2>();

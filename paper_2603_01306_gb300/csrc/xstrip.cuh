@@ -74,6 +74,7 @@ struct XSArgs {
   double rowl1;               // max_i ||x_i||_1 of the stored X (NaN when X holds a NaN)
   double* g;             // [Gr][NB][p] X' r per row group
   double* lterm;         // [n][2] per-row {F, -F*(-zeta)} (certification links) or NULL
+  double* lterm2;        // [n][2] the same at the second dual point (LINK_CERT2_*) or NULL
   unsigned* cnt;         // [nblk] CTAs done with the block's dots (zeroed before the launch)
   int* status;
   uint64_t limit_ns;
@@ -204,7 +205,8 @@ __device__ __forceinline__ void butterfly16(double (&h)[16], int lane) {
 // the float-float and FP64 passes keep it in FP64.
 template <int NF, int NB, bool LOWP = false>
 __device__ __forceinline__ void link_of(int link, const double* z, double yd, double zp, double mom, double* w,
-                                        double& lf, double& ld) {
+                                        double& lf, double& ld, double& ld2) {
+  ld2 = 0.0;
 #pragma unroll
   for (int q = 0; q < NB; ++q) w[q] = 0.0;
   lf = 0.0;
@@ -247,6 +249,24 @@ __device__ __forceinline__ void link_of(int link, const double* z, double yd, do
       w[0] = -yd / (1.0 + exp(yd * zd));
       lf = softplus_neg(yd * z[0]);
       ld = entropy_of(yd * zd);
+      break;
+    }
+    case LINK_CERT2_LS: {
+      const double d0 = z[0] - yd, d1 = zp - yd;
+      w[0] = 2.0 * d1;
+      if (NB > 1) w[NB - 1] = 2.0 * d0;
+      const double zeta1 = -2.0 * d1, zeta0 = -2.0 * d0;
+      lf = d0 * d0;
+      ld = zeta1 * yd - 0.25 * zeta1 * zeta1;
+      ld2 = zeta0 * yd - 0.25 * zeta0 * zeta0;
+      break;
+    }
+    case LINK_CERT2_LOGI: {
+      w[0] = -yd / (1.0 + exp(yd * zp));
+      if (NB > 1) w[NB - 1] = -yd / (1.0 + exp(yd * z[0]));
+      lf = softplus_neg(yd * z[0]);
+      ld = entropy_of(yd * zp);
+      ld2 = entropy_of(yd * z[0]);
       break;
     }
     default: break;
@@ -536,7 +556,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           if constexpr (FF) accl[q][t][l] = 0.f;
           else if constexpr (kF32) { ahi[q][t][l] = 0.f; alo[q][t][l] = 0.f; }
         }
-    const bool need_zp = a.link == LINK_CERTZ_LS || a.link == LINK_CERTZ_LOGI || (a.link == LINK_LOGISTIC && NB > 1);
+    const bool need_zp = a.link == LINK_CERTZ_LS || a.link == LINK_CERTZ_LOGI || a.link == LINK_CERT2_LS ||
+                         a.link == LINK_CERT2_LOGI || (a.link == LINK_LOGISTIC && NB > 1);
     const double* zprev = static_cast<const double*>(a.ps->zprev);
     double* zout = static_cast<double*>(a.ps->zout);
     const double mom = a.ps->mom;
@@ -566,8 +587,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       double z[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) z[f] = (double)(long long)__ldcg(&a.zfix[(size_t)f * n + rowj]) * zinv[f];
-      double rv[NB], lf, ld;
-      link_of<NF, NB, kF32 && !FF>(a.link, z, yd, zp, mom, rv, lf, ld);
+      double rv[NB], lf, ld, ld2;
+      link_of<NF, NB, kF32 && !FF>(a.link, z, yd, zp, mom, rv, lf, ld, ld2);
       if (jl >= rows) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) rv[q] = 0.0;   // rows past the end carry weight 0
@@ -584,6 +605,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       if (cc == k % a.Gc && hb == 0 && jl < rows) {   // this CTA records the block
         if (zout) zout[r0 + jl] = z[0];
         if (a.lterm) { a.lterm[2 * (r0 + jl)] = lf; a.lterm[2 * (r0 + jl) + 1] = ld; }
+        if (a.lterm2) { a.lterm2[2 * (r0 + jl)] = lf; a.lterm2[2 * (r0 + jl) + 1] = ld2; }
       }
       if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullB[st], (k / a.SB) & 1, a.limit_ns, a.status))) {
         tmo = 1;
