@@ -415,6 +415,8 @@ XSArgs pass_args(relax_handle* h, const XSPlan& pl, int link, PassState* ps) {
   a.nblk = pl.nblk;
   a.SA = pl.SA;
   a.SB = pl.SB;
+  a.RA = pl.RA;
+  a.RB = pl.RB;
   a.lag = pl.lag;
   a.link = link;
   a.y = (const double*)h->y;
@@ -931,8 +933,9 @@ relax_status relax_create(relax_handle** out, const void* X, const void* y, int6
     }
     if (std::getenv("RELAX_DEBUG")) {
       const XSPlan& q = h->pl_loop;
-      std::fprintf(stderr, "[relax] loop pass: xk=%d Gc=%d Gr=%d sw=%lld (%d x %d) B=%d nblk=%d SA=%d SB=%d lag=%d threads=%d smem=%zu\n",
-                   q.xk, q.Gc, q.Gr, (long long)q.sw, q.nbox, q.inner, q.B, q.nblk, q.SA, q.SB, q.lag, q.threads, q.smem);
+      std::fprintf(stderr, "[relax] loop pass: xk=%d Gc=%d Gr=%d sw=%lld (%d x %d) B=%d nblk=%d SA=%d SB=%d RA=%d RB=%d lag=%d threads=%d smem=%zu\n",
+                   q.xk, q.Gc, q.Gr, (long long)q.sw, q.nbox, q.inner, q.B, q.nblk, q.SA, q.SB, q.RA, q.RB, q.lag, q.threads,
+                   q.smem);
     }
     // FP32, BF16 and FP8 data: the loop's per-coordinate arithmetic in FP32
     // (FP64 at a small fraction of the FP32 rate on this GPU); FP64 data keeps

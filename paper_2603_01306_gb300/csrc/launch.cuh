@@ -25,6 +25,7 @@ struct XSPlan {
   int inner = 1, nbox = 1, boxb = 128;
   int B = 1, nblk = 1;     // rows per block, blocks
   int SA = 3, SB = 3, lag = 4;
+  int RA = 3, RB = 3;       // ring stages, multiples of SA / SB
   int grid = 1, threads = 32;
   size_t smem = 0;
   const void* kernel = nullptr;

@@ -103,6 +103,40 @@ __device__ __forceinline__ double entropy_of(double t) {
 // Compensated accumulation of FP32 partial sums into an (hi, lo) FP32 pair
 // (Knuth's TwoSum): hi + lo carries the running sum to about twice the FP32
 // precision without FP64 arithmetic.
+// Packed FP32 pairs: Blackwell's f32x2 add / sub / fma issue one instruction
+// for two independent FP32 operations, each rounded exactly as the scalar
+// instruction rounds it (IEEE round to nearest even).
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+  return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 f2_of(unsigned long long b) {
+  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+// a * b + c per half
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return f2_of(r);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_of(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_of(r);
+}
+// two_sum_acc (below) on both halves of a pair
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 a) {
+  const float2 s = add2(hi, a);
+  const float2 bp = sub2(s, hi);
+  const float2 err = add2(sub2(hi, sub2(s, bp)), sub2(a, bp));
+  hi = s;
+  lo = add2(lo, err);
+}
+
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float a) {
   const float s = hi + a;
   const float bp = s - hi;

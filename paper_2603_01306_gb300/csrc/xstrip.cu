@@ -44,10 +44,11 @@ static int xs_tv(int vec) { return vec == 2 ? 6 : vec == 4 ? 6 : vec == 8 ? 3 : 
 //    row), chosen to keep the most SMs busy (Gc strips x Gr row groups), at
 //    least 2 KB wide where possible;
 //  * a strip is nbox tensor boxes of `inner` <= 256 columns;
-//  * blocks of B <= 16 rows so that a stage is about 40 KB; 3 + 3 stages;
+//  * blocks of B <= 16 rows so that a stage is about 40 KB; 3 + 3 warps and
+//    as many stages per warp as shared memory holds (ring A first);
 //  * phase A may lead phase B by `lag` blocks: about 64 MB of X in L2 (at
 //    least 20 blocks with four or more row groups).
-// RELAX_XS="B,SA,SB,lag,vps" overrides for tuning runs (0 keeps a default).
+// RELAX_XS="B,SA,SB,lag,vps,mA,mB" overrides for tuning runs (0 keeps a default).
 cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t n, int64_t p) {
   pl = XSPlan{};
   pl.xk = xk;
@@ -62,9 +63,9 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int es = xkind_esize(xk);
   const int vec = xkind_vec(xk);
-  int B_f = 0, SA_f = 0, SB_f = 0, lag_f = 0, vps_f = 0;
+  int B_f = 0, SA_f = 0, SB_f = 0, lag_f = 0, vps_f = 0, mA_f = 0, mB_f = 0;
   if (const char* ov = std::getenv("RELAX_XS"))
-    std::sscanf(ov, "%d,%d,%d,%d,%d", &B_f, &SA_f, &SB_f, &lag_f, &vps_f);
+    std::sscanf(ov, "%d,%d,%d,%d,%d,%d,%d", &B_f, &SA_f, &SB_f, &lag_f, &vps_f, &mA_f, &mB_f);
   // strips: over the number of row groups Gr, the strip width (at most `cap`
   // vectors) that keeps the most SMs busy, strips under 2 KB counted as
   // streaming less efficiently
@@ -107,6 +108,21 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   if (SA_f > 0) SA = std::min(SA_f, XS_MAXS);
   if (SB_f > 0) SB = std::min(SB_f, XS_MAXS);
   if (2 + SA + SB > XS_MAXT / 32 || !fits(B, SA, SB)) return cudaErrorNotSupported;
+  // ring depths: stages per warp.  A stage is held from its TMA issue until
+  // its warp has read the block, so small blocks (narrow element types) need
+  // more of them to keep enough of X in flight; ring A (HBM) first, then
+  // ring B (L2), while shared memory allows
+  int mA = 1, mB = 1;
+  if (mA_f > 0 || mB_f > 0) {
+    mA = std::max(1, mA_f);
+    mB = std::max(1, mB_f);
+  } else {
+    while ((mA + 1) * SA <= XS_MAXR && fits(B, (mA + 1) * SA, mB * SB)) ++mA;
+    if (mA > 1 && (mB + 1) * SB <= XS_MAXR && fits(B, mA * SA, (mB + 1) * SB)) ++mB;
+  }
+  if (mA * SA > XS_MAXR || mB * SB > XS_MAXR || !fits(B, mA * SA, mB * SB)) return cudaErrorNotSupported;
+  pl.RA = mA * SA;
+  pl.RB = mB * SB;
   pl.B = (int)B;
   pl.boxb = (int)boxb(B);
   pl.nblk = (int)((n + B - 1) / B);
@@ -122,7 +138,7 @@ cudaError_t xstrip_plan(XSPlan& pl, int xk, bool f64acc, int NF, int NB, int64_t
   pl.grid = pl.Gc * pl.Gr;
   pl.threads = 32 * (2 + SA + SB);   // two producers, SA dot, SB axpy
   // the combine of the axpy warps' strip sums reuses the rings
-  const size_t ring = (size_t)(SA + SB) * nbox * pl.boxb;
+  const size_t ring = (size_t)(pl.RA + pl.RB) * nbox * pl.boxb;
   const size_t comb = (size_t)SB * NB * pl.sw * sizeof(double);
   pl.smem = std::max(ring, comb) + 128;
   if (pl.smem + 2048 > (size_t)optin) return cudaErrorNotSupported;

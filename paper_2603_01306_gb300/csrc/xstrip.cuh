@@ -12,15 +12,16 @@
 //
 // Per CTA, warp-specialized:
 //  * lane 0 of warp 0 streams the CTA's strip tiles of its blocks from HBM into
-//    ring A (SA stages; a tile is nbox 2-D tensor boxes of B rows x `inner`
-//    columns, loaded by TMA, which zero-fills columns >= p and rows >= n);
-//    lane 0 of warp 1 loads the same tiles again, from L2, into ring B (SB
-//    stages);
-//  * SA "dot" warps (warp a owns stage a of ring A): per row the strip's partial
+//    ring A (RA = mA * SA stages; a tile is nbox 2-D tensor boxes of B rows x
+//    `inner` columns, loaded by TMA, which zero-fills columns >= p and rows
+//    >= n); lane 0 of warp 1 loads the same tiles again, from L2, into ring B
+//    (RB = mB * SB stages);
+//  * SA "dot" warps (warp a owns stages a, a + SA, ... of ring A; block k
+//    goes to stage k mod RA): per row the strip's partial
 //    dot product with beta, added to the row's z in 64-bit fixed point
 //    (integer additions commute, so z does not depend on the arrival order of
 //    the Gc strips), then the block is counted in cnt[b];
-//  * SB "axpy" warps (warp e owns stage e of ring B): once cnt[b] = Gc each
+//  * SB "axpy" warps (warp e owns stages e, e + SB, ... of ring B): once cnt[b] = Gc each
 //    reads z of the block's rows, applies the link and accumulates X' r over
 //    its strip; CTA (k mod Gc) of the row group records z and the loss terms
 //    of the group's k-th block; at the end the axpy warps' strip sums are
@@ -31,7 +32,11 @@
 // dot warps wait for only before their first addition (the HBM stream starts
 // at once).
 // Each stage has exactly one consumer warp, which therefore never waits on a
-// barrier phase more than one ahead of the last one it saw.  Phase A may lead
+// barrier phase more than one ahead of the last one it saw (the reason the
+// ring depths are multiples of the warp counts).  A stage is held from its
+// TMA issue until its warp has read the block, so the stages per ring, not
+// the warps, set the bytes in flight: narrow element types, whose blocks are
+// small, take several stages per warp.  Phase A may lead
 // phase B by at most `lag` blocks of the CTA (L2 footprint).  Every wait is
 // bounded: on expiry the kernel records ST_TIMEOUT, stops issuing and waiting,
 // lets the copies in flight land and returns.
@@ -46,7 +51,8 @@
 
 namespace relax {
 
-constexpr int XS_MAXS = 4;        // stages per ring at most (= warps per phase)
+constexpr int XS_MAXS = 4;        // warps per phase at most
+constexpr int XS_MAXR = 12;       // stages per ring at most
 constexpr int XS_MAXB = 16;       // rows per block at most (one butterfly group)
 constexpr int XS_MAXT = 256;      // 2 + SA + SB warps: at most two per scheduler
 // 16-byte vectors of the strip per lane: a lane holds the same number of
@@ -63,7 +69,8 @@ struct XSArgs {
   int inner, nbox;       // box columns (multiple of the vector width, <= 256); boxes per strip
   int boxb;              // bytes per box in shared memory (B * inner * size, padded to 128)
   int B, nblk;           // rows per block, blocks
-  int SA, SB, lag;       // ring stages; lead of phase A over phase B (blocks)
+  int SA, SB, lag;       // dot / axpy warps; lead of phase A over phase B (blocks)
+  int RA, RB;            // ring stages (multiples of SA / SB)
   int link;
   const double* y;
   const float* colscale;
@@ -284,9 +291,13 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   constexpr int VEC = XTraits<TX>::VEC;
   constexpr int TV = XSShape<VEC>::TV;
   constexpr bool kF32 = sizeof(TA) == 4;
+  // FP32 sums on packed pairs (f32x2): measured faster wherever the pass does
+  // more than one FMA per 4 bytes of X (two right-hand sides, BF16 / FP8
+  // elements); the one-right-hand-side FP32 pass ran 10% slower on pairs
+  constexpr bool kPair = kF32 && !FF && !(sizeof(TX) == 4 && NB == 1);
   static_assert(!FF || (sizeof(TX) == 4 && kF32), "float-float: FP32 X and FP32 pairs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t fullA[XS_MAXS], emptyA[XS_MAXS], fullB[XS_MAXS], emptyB[XS_MAXS];
+  __shared__ __align__(8) uint64_t fullA[XS_MAXR], emptyA[XS_MAXR], fullB[XS_MAXR], emptyB[XS_MAXR];
   __shared__ volatile int tmo;        // a bounded wait expired: stop issuing and waiting
   __shared__ volatile unsigned bcnt;  // blocks finished by phase B in this CTA
   __shared__ int skip;
@@ -295,8 +306,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
     tmo = 0;
     bcnt = 0;
     skip = a.ps->done;
-    for (int s = 0; s < a.SA; ++s) { mbar_init(&fullA[s], 1); mbar_init(&emptyA[s], 1); }
-    for (int s = 0; s < a.SB; ++s) { mbar_init(&fullB[s], 1); mbar_init(&emptyB[s], 1); }
+    for (int s = 0; s < a.RA; ++s) { mbar_init(&fullA[s], 1); mbar_init(&emptyA[s], 1); }
+    for (int s = 0; s < a.RB; ++s) { mbar_init(&fullB[s], 1); mbar_init(&emptyB[s], 1); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -326,12 +337,12 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   const int kloc = (cr < a.nblk) ? (a.nblk - cr + a.Gr - 1) / a.Gr : 0;   // blocks of this CTA
   const size_t stage = (size_t)a.nbox * a.boxb;
   unsigned char* ringA = smem;
-  unsigned char* ringB = smem + (size_t)a.SA * stage;
+  unsigned char* ringB = smem + (size_t)a.RA * stage;
   {
     // the fixed-shape row loops read every row of a tile; keep never-loaded
     // stage memory finite
     float4* z4 = reinterpret_cast<float4*>(smem);
-    const size_t nz = (size_t)(a.SA + a.SB) * stage / 16;
+    const size_t nz = (size_t)(a.RA + a.RB) * stage / 16;
     for (size_t i = tid; i < nz; i += blockDim.x) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
   }
@@ -347,9 +358,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       const uint64_t pol = policy_evict_normal();
       int issued = 0;
       for (int k = 0; k < kloc; ++k) {
-        const int s = k % a.SA;
+        const int s = k % a.RA;
         if (tmo) break;
-        if (k >= a.SA && !mbar_wait<false>(&emptyA[s], ((k / a.SA) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
+        if (k >= a.RA && !mbar_wait<false>(&emptyA[s], ((k / a.RA) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
         if (k > a.lag && !wait_smem(&bcnt, (unsigned)(k - a.lag), a.limit_ns, a.status)) { tmo = 1; break; }
         const int y0 = (cr + k * a.Gr) * a.B;
         mbar_arrive_expect_tx(&fullA[s], tilebytes);
@@ -358,8 +369,8 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         issued = k + 1;
       }
       // let every copy in flight land before the CTA may exit
-      for (int k = (issued > a.SA ? issued - a.SA : 0); k < issued; ++k)
-        mbar_wait<false>(&fullA[k % a.SA], (k / a.SA) & 1, a.limit_ns, a.status);
+      for (int k = (issued > a.RA ? issued - a.RA : 0); k < issued; ++k)
+        mbar_wait<false>(&fullA[k % a.RA], (k / a.RA) & 1, a.limit_ns, a.status);
     }
   } else if (warp == 1) {
     // ---------------------------------- producer B: L2 -> ring B (its own warp,
@@ -368,17 +379,17 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       const uint64_t pol = policy_evict_first();
       int issued = 0;
       for (int k = 0; k < kloc; ++k) {
-        const int s = k % a.SB;
+        const int s = k % a.RB;
         if (tmo) break;
-        if (k >= a.SB && !mbar_wait<false>(&emptyB[s], ((k / a.SB) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
+        if (k >= a.RB && !mbar_wait<false>(&emptyB[s], ((k / a.RB) - 1) & 1, a.limit_ns, a.status)) { tmo = 1; break; }
         const int y0 = (cr + k * a.Gr) * a.B;
         mbar_arrive_expect_tx(&fullB[s], tilebytes);
         for (int i = 0; i < a.nbox; ++i)
           tma_load_2d(ringB + s * stage + (size_t)i * a.boxb, &a.tm, (int)s0 + i * a.inner, y0, &fullB[s], pol);
         issued = k + 1;
       }
-      for (int k = (issued > a.SB ? issued - a.SB : 0); k < issued; ++k)
-        mbar_wait<false>(&fullB[k % a.SB], (k / a.SB) & 1, a.limit_ns, a.status);
+      for (int k = (issued > a.RB ? issued - a.RB : 0); k < issued; ++k)
+        mbar_wait<false>(&fullB[k % a.RB], (k / a.RB) & 1, a.limit_ns, a.status);
     }
   } else if (warp < 2 + a.SA) {
     // ------------------------------------------------ phase A: strip dot products
@@ -431,14 +442,15 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
     bool have_scale = false;
     for (int k = st; k < kloc; k += a.SA) {
       if (tmo) break;
-      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullA[st], (k / a.SA) & 1, a.limit_ns, a.status))) {
+      const int sa = k % a.RA;   // one of this warp's stages
+      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullA[sa], (k / a.RA) & 1, a.limit_ns, a.status))) {
         tmo = 1;
         break;
       }
       const int b = cr + k * a.Gr;
       const int64_t r0 = (int64_t)b * a.B;
       const int rows = (int)((n - r0) < a.B ? (n - r0) : a.B);
-      const unsigned char* tile = ringA + st * stage;
+      const unsigned char* tile = ringA + sa * stage;
       // per-lane partials of the block's rows (plain FP32 over the lane's
       // columns), then one transposed butterfly per forward vector
       TA ph[NF][XS_MAXB];
@@ -480,21 +492,40 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         for (int f = 0; f < NF; ++f) ph[f][jj] = (TA)0;
         const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
         const unsigned char* rowp = tile + (size_t)jr * rowpitch;
+        if constexpr (kPair) {
+          // FP32: even and odd columns in the two halves of a packed pair
+          float2 p2[NF];
 #pragma unroll
-        for (int t = 0; t < TV; ++t) {
-          TA x[VEC];
-          XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+          for (int f = 0; f < NF; ++f) p2[f] = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int f = 0; f < NF; ++f)
+          for (int t = 0; t < TV; ++t) {
+            TA x[VEC];
+            XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int l = 0; l < VEC; l += 2)
+                p2[f] = fma2(make_float2(x[l], x[l + 1]), make_float2(bv[f][t][l], bv[f][t][l + 1]), p2[f]);
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) ph[f][jj] = p2[f].x + p2[f].y;
+        } else {
+#pragma unroll
+          for (int t = 0; t < TV; ++t) {
+            TA x[VEC];
+            XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int l = 0; l < VEC; ++l) ph[f][jj] += x[l] * bv[f][t][l];
+          }
         }
       }
       }
       // every read of the stage is done (the partials are in registers):
       // hand it back to the producer before the butterfly
       __syncwarp();
-      if (lane == 0) mbar_arrive(&emptyA[st]);
+      if (lane == 0) mbar_arrive(&emptyA[sa]);
       // lane 2j: the strip partial of row j, as (hi, lo)
       TA mh[NF], ml[NF];
 #pragma unroll
@@ -607,12 +638,16 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         if (a.lterm) { a.lterm[2 * (r0 + jl)] = lf; a.lterm[2 * (r0 + jl) + 1] = ld; }
         if (a.lterm2) { a.lterm2[2 * (r0 + jl)] = lf; a.lterm2[2 * (r0 + jl) + 1] = ld2; }
       }
-      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullB[st], (k / a.SB) & 1, a.limit_ns, a.status))) {
+      const int sb = k % a.RB;   // one of this warp's stages
+      if (!__all_sync(0xffffffffu, mbar_wait<false>(&fullB[sb], (k / a.RB) & 1, a.limit_ns, a.status))) {
         tmo = 1;
         break;
       }
-      const unsigned char* tile = ringB + st * stage;
-#pragma unroll(FF ? 1 : XS_MAXB)
+      const unsigned char* tile = ringB + sb * stage;
+      // rows four at a time (the accumulators are indexed by column only): a
+      // fully unrolled block of rows ran slower, its loop and the dot warps'
+      // sharing the schedulers' instruction caches
+#pragma unroll(FF ? 1 : 4)
       for (int j = 0; j < XS_MAXB; ++j) {
         const int jr = j < a.B ? j : a.B - 1;   // rows >= rows carry weight 0
         TA w[NB];
@@ -627,6 +662,19 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
         for (int t = 0; t < TV; ++t) {
           TA x[VEC];
           XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+          if constexpr (kPair) {
+            // two columns per packed FP32 FMA (the same roundings as two scalar FMAs)
+#pragma unroll
+            for (int l = 0; l < VEC; l += 2)
+#pragma unroll
+              for (int q = 0; q < NB; ++q) {
+                const float2 r2 = fma2(make_float2(w[q], w[q]), make_float2(x[l], x[l + 1]),
+                                       make_float2(acc[q][t][l], acc[q][t][l + 1]));
+                acc[q][t][l] = r2.x;
+                acc[q][t][l + 1] = r2.y;
+              }
+            continue;
+          }
 #pragma unroll
           for (int l = 0; l < VEC; ++l)
 #pragma unroll
@@ -646,7 +694,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       }
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&emptyB[st]);
+        mbar_arrive(&emptyB[sb]);
         atomicAdd((unsigned*)&bcnt, 1u);
       }
       if constexpr (kF32 && !FF) {   // fold the block's FP32 sums into the compensated pair
@@ -655,9 +703,23 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
 #pragma unroll
           for (int t = 0; t < TV; ++t)
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) {
-              two_sum_acc(ahi[q][t][l], alo[q][t][l], (float)acc[q][t][l]);
+            for (int l = 0; l < VEC; l += 2) {
+              if constexpr (!kPair) {
+                two_sum_acc(ahi[q][t][l], alo[q][t][l], (float)acc[q][t][l]);
+                two_sum_acc(ahi[q][t][l + 1], alo[q][t][l + 1], (float)acc[q][t][l + 1]);
+                acc[q][t][l] = (TA)0;
+                acc[q][t][l + 1] = (TA)0;
+                continue;
+              }
+              float2 h2 = make_float2(ahi[q][t][l], ahi[q][t][l + 1]);
+              float2 l2 = make_float2(alo[q][t][l], alo[q][t][l + 1]);
+              two_sum_acc2(h2, l2, make_float2((float)acc[q][t][l], (float)acc[q][t][l + 1]));
+              ahi[q][t][l] = h2.x;
+              ahi[q][t][l + 1] = h2.y;
+              alo[q][t][l] = l2.x;
+              alo[q][t][l + 1] = l2.y;
               acc[q][t][l] = (TA)0;
+              acc[q][t][l + 1] = (TA)0;
             }
       }
     }

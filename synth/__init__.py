@@ -162,6 +162,10 @@ WORKLOADS = {
                                         extra={"nodes": 256, "j0_max": 40, "j1_max": 19}),
     "logistic_100000x20000_lowp": Workload("logistic_100000x20000_lowp", 100000, 20000,
                                            0.5, 30, 0.1, "logistic", 5.0),
+    # the same recipe on a quarter of the rows (2 GB of FP32 X, 1 GB as BF16):
+    # the case counter captures of the quantized passes run on
+    "logistic_25000x20000_lowp": Workload("logistic_25000x20000_lowp", 25000, 20000,
+                                          0.5, 30, 0.1, "logistic", 5.0),
     "bnb_2000x5000_f32": Workload("bnb_2000x5000_f32", 2000, 5000, 0.8, 15, 0.2, "ls",
                                   5.0),
 }
