@@ -167,6 +167,28 @@ __device__ __forceinline__ void pair_add(float& h, float& l, float rh, float rl)
   l = l + rl + e;
 }
 
+// Steps of a transposed butterfly over N = 2^m rows, at lane strides o0,
+// o0/2, ...: each step sends half of the remaining rows to the partner lane
+// and keeps the other half (the upper half on lanes with the stride's bit
+// set); afterwards h[0], l[0] hold the sum over those m lane bits of the row
+// whose index bits, high to low, are the lane's bits o0, o0/2, ...
+template <int N>
+__device__ __forceinline__ void bfly_steps(float (&h)[N], float (&l)[N], int lane, int o0) {
+#pragma unroll
+  for (int half = N / 2, o = o0; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float sh = up ? h[i] : h[i + half], sl = up ? l[i] : l[i + half];
+      const float kh = up ? h[i + half] : h[i], kl = up ? l[i + half] : l[i];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      h[i] = kh;
+      l[i] = kl;
+      pair_add(h[i], l[i], rh, rl);
+    }
+  }
+}
+
 // Transposed butterfly over 16 rows: on entry lane L holds its partial of
 // every row in h[0..15] (l = low parts); on exit h[0], l[0] of lane L hold the
 // warp total of row (L >> 1) & 15.  Each step sends half of the remaining rows
@@ -295,6 +317,9 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
   // more than one FMA per 4 bytes of X (two right-hand sides, BF16 / FP8
   // elements); the one-right-hand-side FP32 pass ran 10% slower on pairs
   constexpr bool kPair = kF32 && !FF && !(sizeof(TX) == 4 && NB == 1);
+  // FP8 (16 elements per vector): the dot warps' rows in a rolled loop of
+  // four-row groups (measured faster there, slower for FP32 and BF16)
+  constexpr bool kGroup = kPair && sizeof(TX) == 1;
   static_assert(!FF || (sizeof(TX) == 4 && kF32), "float-float: FP32 X and FP32 pairs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t fullA[XS_MAXR], emptyA[XS_MAXR], fullB[XS_MAXR], emptyB[XS_MAXR];
@@ -455,6 +480,7 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
       // columns), then one transposed butterfly per forward vector
       TA ph[NF][XS_MAXB];
       float phl[FF ? NF : 1][XS_MAXB];   // FF: low parts
+      float vh[NF][4], vl[NF][4];        // kGroup: the four row groups after two butterfly steps
       if constexpr (FF) {
         // float-float: one row at a time (the fully unrolled block of
         // float-float sums outgrew the instruction cache); the row partials
@@ -484,6 +510,61 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           }
 #pragma unroll
           for (int f = 0; f < NF; ++f) { ph[f][jj] = hh[f]; phl[f][jj] = ll[f]; }
+        }
+      } else if constexpr (kGroup) {
+        // FP32 sums, rows in four groups of four (a rolled loop, for the
+        // schedulers' instruction caches): group g holds rows g, g+4, g+8,
+        // g+12, whose partials take the butterfly's first two steps (lane
+        // strides 16, 8) in the group and the last ones (4, 2, 1) after the
+        // loop -- the additions of the 16-row butterfly, in its order
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+          float gh[NF][4], gl[NF][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int jj = g + 4 * i;
+            const int jr = jj < a.B ? jj : a.B - 1;   // rows >= rows: zero-filled or repeated, discarded
+            const unsigned char* rowp = tile + (size_t)jr * rowpitch;
+            if constexpr (kPair) {
+              // even and odd columns in the two halves of a packed pair
+              float2 p2[NF];
+#pragma unroll
+              for (int f = 0; f < NF; ++f) p2[f] = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int t = 0; t < TV; ++t) {
+                TA x[VEC];
+                XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                  for (int l = 0; l < VEC; l += 2)
+                    p2[f] = fma2(make_float2(x[l], x[l + 1]), make_float2(bv[f][t][l], bv[f][t][l + 1]), p2[f]);
+              }
+#pragma unroll
+              for (int f = 0; f < NF; ++f) gh[f][i] = p2[f].x + p2[f].y;
+            } else {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) gh[f][i] = 0.f;
+#pragma unroll
+              for (int t = 0; t < TV; ++t) {
+                TA x[VEC];
+                XTraits<TX>::load(reinterpret_cast<const TX*>(rowp + voff[t]), x);
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                  for (int l = 0; l < VEC; ++l) gh[f][i] += x[l] * bv[f][t][l];
+              }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) gl[f][i] = 0.f;
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            bfly_steps<4>(gh[f], gl[f], lane, 16);
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg)   // registers, not an indexed array
+              if (gg == g) { vh[f][gg] = gh[f][0]; vl[f][gg] = gl[f][0]; }
+          }
         }
       } else {
 #pragma unroll
@@ -534,6 +615,12 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           butterfly16(ph[f], phl[f], lane);
           mh[f] = ph[f][0];
           ml[f] = phl[f][0];
+        } else if constexpr (kGroup) {
+          bfly_steps<4>(vh[f], vl[f], lane, 4);
+          const float rh = __shfl_xor_sync(0xffffffffu, vh[f][0], 1), rl = __shfl_xor_sync(0xffffffffu, vl[f][0], 1);
+          pair_add(vh[f][0], vl[f][0], rh, rl);
+          mh[f] = vh[f][0];
+          ml[f] = vl[f][0];
         } else if constexpr (kF32) {
           float pl[XS_MAXB];
 #pragma unroll
@@ -673,23 +760,23 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
                 acc[q][t][l] = r2.x;
                 acc[q][t][l + 1] = r2.y;
               }
-            continue;
-          }
+          } else {
 #pragma unroll
-          for (int l = 0; l < VEC; ++l)
+            for (int l = 0; l < VEC; ++l)
 #pragma unroll
-            for (int q = 0; q < NB; ++q) {
-              if constexpr (FF) {
-                const float pr = w[q] * x[l];
-                const float lo = fmaf(wl[q], x[l], fmaf(w[q], x[l], -pr));
-                const float sacc = acc[q][t][l] + pr;
-                const float bp = sacc - acc[q][t][l];
-                accl[q][t][l] += ((acc[q][t][l] - (sacc - bp)) + (pr - bp)) + lo;
-                acc[q][t][l] = sacc;
-              } else {
-                acc[q][t][l] += w[q] * x[l];
+              for (int q = 0; q < NB; ++q) {
+                if constexpr (FF) {
+                  const float pr = w[q] * x[l];
+                  const float lo = fmaf(wl[q], x[l], fmaf(w[q], x[l], -pr));
+                  const float sacc = acc[q][t][l] + pr;
+                  const float bp = sacc - acc[q][t][l];
+                  accl[q][t][l] += ((acc[q][t][l] - (sacc - bp)) + (pr - bp)) + lo;
+                  acc[q][t][l] = sacc;
+                } else {
+                  acc[q][t][l] += w[q] * x[l];
+                }
               }
-            }
+          }
         }
       }
       __syncwarp();
@@ -704,20 +791,18 @@ __global__ void __launch_bounds__(XS_MAXT, 1) xstrip_kernel(const __grid_constan
           for (int t = 0; t < TV; ++t)
 #pragma unroll
             for (int l = 0; l < VEC; l += 2) {
-              if constexpr (!kPair) {
+              if constexpr (kPair) {
+                float2 h2 = make_float2(ahi[q][t][l], ahi[q][t][l + 1]);
+                float2 l2 = make_float2(alo[q][t][l], alo[q][t][l + 1]);
+                two_sum_acc2(h2, l2, make_float2((float)acc[q][t][l], (float)acc[q][t][l + 1]));
+                ahi[q][t][l] = h2.x;
+                ahi[q][t][l + 1] = h2.y;
+                alo[q][t][l] = l2.x;
+                alo[q][t][l + 1] = l2.y;
+              } else {
                 two_sum_acc(ahi[q][t][l], alo[q][t][l], (float)acc[q][t][l]);
                 two_sum_acc(ahi[q][t][l + 1], alo[q][t][l + 1], (float)acc[q][t][l + 1]);
-                acc[q][t][l] = (TA)0;
-                acc[q][t][l + 1] = (TA)0;
-                continue;
               }
-              float2 h2 = make_float2(ahi[q][t][l], ahi[q][t][l + 1]);
-              float2 l2 = make_float2(alo[q][t][l], alo[q][t][l + 1]);
-              two_sum_acc2(h2, l2, make_float2((float)acc[q][t][l], (float)acc[q][t][l + 1]));
-              ahi[q][t][l] = h2.x;
-              ahi[q][t][l + 1] = h2.y;
-              alo[q][t][l] = l2.x;
-              alo[q][t][l + 1] = l2.y;
               acc[q][t][l] = (TA)0;
               acc[q][t][l + 1] = (TA)0;
             }
