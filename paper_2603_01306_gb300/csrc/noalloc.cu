@@ -29,9 +29,11 @@ namespace {
 // address comes from cudaGetSymbolAddress.
 constexpr size_t kScratchBytes = 64 * 1024;
 static __device__ __align__(256) unsigned char g_prox_scratch[kScratchBytes];
-// The launch uses at most ceil(p / 512) blocks of 160 bytes of partials each,
-// after 3 * 256 * 8 bytes of accumulators and 64 bytes of counters: the
-// largest p whose scratch is sure to fit.
+// Each block of the launch takes 160 bytes of partials, after 3 * 256 * 8
+// bytes of accumulators and 64 bytes of counters.  kMaxP is the largest p for
+// which ceil(p / 512) blocks fit; the launch's own grid (one element per
+// thread while all its blocks fit the GPU at once, else more) is checked
+// against the array again before the launch.
 constexpr int64_t kMaxP = (int64_t)((kScratchBytes - 3 * ACC_STRIDE * 8 - 64) / (2 * NBP * 8)) * (2 * PBLOCK);
 
 constexpr int kMaxDevices = 64;

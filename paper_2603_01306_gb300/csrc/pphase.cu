@@ -1,5 +1,6 @@
 // Instantiations and cooperative launch of the p-phase kernel.
 #include <algorithm>
+#include <cstdlib>
 
 #include "launch.cuh"
 
@@ -21,8 +22,13 @@ cudaError_t pphase_plan(PPlan& pl, bool vdouble, int64_t p, bool backtrack, bool
   if (e != cudaSuccess) return e;
   const int64_t maxgrid = (int64_t)nsm * std::max(per, 1);
   pl.maxgrid = (int)maxgrid;
-  // about two elements per thread; at most PEPT
-  const int64_t want = (p + 2 * PBLOCK - 1) / (2 * PBLOCK);
+  // one element per thread where the co-resident grid allows (measured at
+  // p = 50000: 1 -> 0.080 ms per iteration, 2 -> 0.084, 4 -> 0.099: the
+  // grid barriers cost less than the longer per-thread chains), at most
+  // PEPT (RELAX_PP=e sets e elements per thread for tuning runs)
+  int ept = 1;
+  if (const char* ov = std::getenv("RELAX_PP")) ept = std::max(1, std::min(PEPT, std::atoi(ov)));
+  const int64_t want = (p + (int64_t)ept * PBLOCK - 1) / ((int64_t)ept * PBLOCK);
   int64_t g = std::max<int64_t>(1, std::min<int64_t>(want, maxgrid));
   if (g * PBLOCK * PEPT < p) g = (p + (int64_t)PBLOCK * PEPT - 1) / ((int64_t)PBLOCK * PEPT);
   if (g > maxgrid) return cudaErrorNotSupported;
