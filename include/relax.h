@@ -150,14 +150,19 @@ relax_status relax_create(relax_handle** h, const void* X, const void* y, int64_
  *   out: host; filled on every return path after argument validation, including
  *      RELAX_ENOTCONV / RELAX_ETIMEOUT (dual_bound stays a valid bound).
  * The loop stops when its own gap estimate reaches gap_tol (0.7 gap_tol when X
- * is FP32 or narrower, where that estimate is not FP64).  The FP64
+ * is FP32 or narrower, where that estimate is not FP64; a loop on BF16 / FP8
+ * storage stops at 1e-3 / 1e-2, about its format's effect on the bound).  The
  * certificate then evaluates Phi at the best primal iterate and Psi at two
- * dual points (the loop's best one, and zeta = -grad F(X beta_best) formed in
- * FP64) and keeps the better bound; it decides the status.  When it misses
+ * dual points (the loop's best one, and zeta = -grad F(X beta_best)) in one
+ * pass over the full-precision X (FP64 for FP64 data, float-float for FP32
+ * data) and keeps the better bound; it decides the status.  When it misses
  * gap_tol the loop resumes with a 4x tighter target for at most half as many
  * iterations again, at most 3 times and only while the certified gap keeps
- * shrinking; with BF16/FP8 storage it does not resume (that gap is the
- * quantisation's, reported through RELAX_ENOTCONV with a valid bound).
+ * shrinking.  When the loop's arithmetic is what stops it (the loop stalled,
+ * or it read the BF16 / FP8 copy), the solve climbs the precision ladder
+ * (relax_result.ladder): the loop goes on from beta_best on the FP32 X, then
+ * with float-float products; a gap still above gap_tol after that is
+ * reported through RELAX_ENOTCONV with a valid bound.
  * Synchronizes the handle's stream. */
 relax_status relax_solve(relax_handle* h, const int8_t* fixings, const void* warm_start,
                          double gap_tol, void* beta_out, relax_result* out);
@@ -233,9 +238,11 @@ relax_status relax_watchdog_probe(int32_t watchdog_ms, double* waited_ms, void* 
 relax_status relax_xpass(relax_handle* h, const void* beta, void* z_out, void* g_out,
                          double* loss_host);
 
-/* FP64 evaluation of Phi(beta_primal) (Eq. 6) and Psi(zeta) (Eq. 7) at
- * zeta = -grad F(X beta_dual), with the full-precision X (certification).
+/* FP64-grade evaluation of Phi(beta_primal) (Eq. 6) and Psi(zeta) (Eq. 7) at
+ * zeta = -grad F(X beta_dual), with the full-precision X (certification:
+ * FP64 passes for FP64 data, float-float products and sums for FP32 data).
  *   beta_primal, beta_dual: device p (handle dtype); fixings as in relax_solve.
+ *   The same pointer for both points takes one product of X instead of two.
  *   out_host: host double[2] = {Phi, Psi}.  Phi is +inf when beta_primal is
  *   outside dom g_N.  Synchronizes the handle's stream. */
 relax_status relax_certify(relax_handle* h, const int8_t* fixings, const void* beta_primal,
