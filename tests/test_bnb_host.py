@@ -142,3 +142,50 @@ def test_bnb_is_not_certified_when_the_node_budget_runs_out(batch):
     assert st.nodes <= 3
     assert not st.certified
     assert st.best_bound <= st.incumbent
+
+
+def test_batched_bnb_reaches_the_optimum_and_solves_each_support_once():
+    """The batched driver (children of several open nodes per call) reaches
+    the brute-force k-sparse optimum, certified; its incumbent heuristic
+    solves every candidate support once (later candidates with a support
+    already solved reuse its objective)."""
+    import torch
+    from oracle import brute
+    from paper_2603_01306_gb300 import bnb
+    import synth
+    # a weak signal (SNR 1) on 30 x 12, k = 3: 37 nodes, and candidate
+    # supports that repeat across the tree
+    X = synth.ar1_design(30, 12, 0.5, 1)
+    y = synth.response(synth.signal_from_design(X, 3), "ls", 1.0, 1)
+    k, lam2, M = 3, 0.05, 2.0
+    h = _OracleHandle(X, y, k, lam2, M)
+    incumbent_supports = []
+    candidates = []
+    fix_of = bnb._incumbent_fix
+
+    def solve_batch(nb, fixings=None, warm_start=None, gap_tol=1e-6, beta_out=None):
+        if h.cut == float("inf"):   # the incumbent heuristic's solves run without a cutoff
+            incumbent_supports.extend(np.flatnonzero(fixings[i].cpu().numpy() > 0).tobytes() for i in range(nb))
+        outs = [h.solve(fixings[i], None if warm_start is None else warm_start[i], gap_tol) for i in range(nb)]
+        return torch.stack([o[0] for o in outs]), [o[1] for o in outs], 0
+    h.solve_batch = solve_batch
+
+    def counting_fix(beta, fix, kk):
+        f = fix_of(beta, fix, kk)
+        candidates.append(np.flatnonzero(f > 0).tobytes())
+        return f
+    bnb._incumbent_fix = counting_fix
+    try:
+        st = bnb.run(h, k, max_nodes=400, gap_tol=1e-9, batch=4)
+    finally:
+        bnb._incumbent_fix = fix_of
+    opt = brute.ksparse_opt(X, y, "ls", k, lam2, M)
+    assert st.certified and not st.dropped
+    assert st.incumbent == pytest.approx(opt, rel=1e-7)
+    assert st.best_bound == st.incumbent
+    assert len(incumbent_supports) == len(set(incumbent_supports))   # no support solved twice
+    assert st.incumbent_solves == len(incumbent_supports) + 1         # + the root's, solved alone
+    assert len(incumbent_supports) >= 5
+    # every distinct candidate support was solved exactly once (the root's alone)
+    assert set(incumbent_supports) <= set(candidates)
+    assert len(set(candidates)) == len(incumbent_supports) + 1
